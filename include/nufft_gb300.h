@@ -1,0 +1,183 @@
+/*
+ * nufft_gb300.h -- C ABI of a GB300 (sm_103a) implementation of the type-1 and
+ * type-2 non-uniform FFT with the "exponential of semicircle" (ES) kernel of
+ * Barnett, Magland & af Klinteberg, arXiv:1808.06736.
+ *
+ * Transforms (Sec. 1, Eq. (1) and Eq. (2)), with the sign flag isign = +1 or -1:
+ *   type 1 (non-uniform to uniform):  f_k = sum_{j=1..M} c_j exp(i isign k.x_j),  k in I_N
+ *   type 2 (uniform to non-uniform):  c_j = sum_{k in I_N} f_k exp(i isign k.x_j), j = 1..M
+ * computed to relative tolerance eps by spreading / interpolation with the ES
+ * kernel on a 2x upsampled grid, an FFT and a diagonal correction (Sec. 3).
+ * I_N = I_{N_1} x ... x I_{N_d}, I_{N_i} = {-floor(N_i/2), ..., N_i - 1 - floor(N_i/2)}.
+ * The type-2 transform with sign -isign is the adjoint of the type-1 transform
+ * with sign isign.
+ *
+ * Conventions shared by every entry point:
+ *  - Points x_j, y_j, z_j are given in radians; the transforms are 2 pi
+ *    periodic, so any finite value is accepted (opts.chkbnds = 1 restricts
+ *    them to [-3 pi, 3 pi], as Sec. 2 describes).
+ *  - Complex arrays are interleaved (re, im): float pairs for NUFFT_C64,
+ *    double pairs for NUFFT_C128.  Point arrays are float resp. double.
+ *  - Mode arrays f hold N_1 * ... * N_d values, dimension 1 fastest, each
+ *    dimension in increasing k (opts.modeord = 0) or in FFT order
+ *    0, 1, ..., -1 (opts.modeord = 1).
+ *  - Every pointer handed to nufft_setpts / nufft_execute is DEVICE memory on
+ *    the plan's device; the caller keeps ownership.  All device work is
+ *    enqueued on the plan's CUDA stream and is asynchronous with respect to
+ *    the host; nufft_get_status / nufft_get_timings synchronise that stream.
+ *  - Return values: 0 success, > 0 warning (the call still did its work),
+ *    < 0 error (the call did nothing further).  nufft_strerror names them.
+ *  - A plan is not thread-safe; use one plan per host thread.
+ */
+#ifndef NUFFT_GB300_H
+#define NUFFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* precision selector for nufft_makeplan */
+#define NUFFT_C64 1  /* complex64 data, float points, float arithmetic   */
+#define NUFFT_C128 2 /* complex128 data, double points, double arithmetic */
+
+/* status codes */
+#define NUFFT_OK 0
+#define NUFFT_WARN_EPS_TOO_SMALL 1   /* eps below what the precision (or w <= 16) can deliver */
+#define NUFFT_ERR_BAD_ARG (-1)       /* invalid type, dim, N_i, isign, ntransf, eps, M, prec or NULL pointer */
+#define NUFFT_ERR_OUT_OF_RANGE (-2)  /* opts.chkbnds = 1 and a point lies outside [-3 pi, 3 pi] (or is not finite) */
+#define NUFFT_ERR_ALLOC (-3)         /* device allocation failed */
+#define NUFFT_ERR_CUDA (-4)          /* a CUDA runtime call or kernel launch failed */
+#define NUFFT_ERR_CUFFT (-5)         /* cuFFT planning or execution failed */
+#define NUFFT_ERR_NOT_SET (-6)       /* nufft_execute before nufft_setpts */
+#define NUFFT_ERR_TOO_BIG (-7)       /* M >= 2^31, or a grid the index types cannot address */
+
+typedef struct nufft_plan_s* nufft_plan;
+
+/*
+ * Options (Sec. 2 describes debug and chkbnds; the rest are GPU tunables).
+ * nufft_default_opts fills every field; 0 in a tunable means "choose".
+ */
+typedef struct {
+  int debug;          /* 1: record CUDA-event timings of every step (nufft_get_timings) */
+  int chkbnds;        /* 1: points outside [-3 pi, 3 pi] make nufft_get_status return NUFFT_ERR_OUT_OF_RANGE */
+  int modeord;        /* 0: increasing k per dimension; 1: FFT order (0..N/2-1 then -N/2..-1) */
+  int bin_size[3];    /* bin extent in fine-grid cells per dimension (0: choose from d, w, precision) */
+  int max_subprob;    /* most points one thread block handles at a time (0: choose) */
+  int threads;        /* threads per block of the spread / interp kernels (0: choose) */
+  int reserved[8];    /* set to zero */
+} nufft_opts;
+
+/* Fill *o with defaults.  Returns NUFFT_OK, or NUFFT_ERR_BAD_ARG for o == NULL. */
+int nufft_default_opts(nufft_opts* o);
+
+/*
+ * Create a plan for ntransf transforms of one type that share the points.
+ *   type      1 or 2.
+ *   dim       1, 2 or 3.
+ *   nmodes    host array of dim mode counts N_i >= 1.
+ *   isign     +1 or -1: the sign of i in the exponent (Sec. 2).
+ *   ntransf   >= 1 vectors per nufft_execute (strided by M resp. N_1...N_d).
+ *   eps       requested relative tolerance > 0.  Sets the kernel width
+ *             w = ceil(log10(1/eps)) + 1 and beta = 2.30 w (Eq. (params)),
+ *             and the fine grid n_i = smallest 2^a 3^b 5^c >= max(2 N_i, 2 w)
+ *             (Sec. 3.1.1).  w is clamped to [2, 16].  eps below 1e-6
+ *             (C64) or 1e-15 (C128) returns NUFFT_WARN_EPS_TOO_SMALL with
+ *             a valid plan: the precision cannot deliver that accuracy.
+ *   prec      NUFFT_C64 or NUFFT_C128.
+ *   stream    a cudaStream_t (NULL = the legacy default stream); the plan uses
+ *             the current CUDA device.
+ *   opts      NULL for defaults.
+ *   out       receives the plan (NULL on error).
+ * Work: computes the correction factors of Eq. (pk) (host, double precision,
+ * Gauss-Legendre rule of Eq. (quad)), allocates the fine grid and plans cuFFT.
+ * Synchronous.  Errors: BAD_ARG, ALLOC, CUDA, CUFFT, TOO_BIG.
+ */
+int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntransf, double eps,
+                   int prec, void* stream, const nufft_opts* opts, nufft_plan* out);
+
+/*
+ * Set the M points (device arrays; y NULL when dim < 2, z NULL when dim < 3).
+ * Folds each coordinate onto the fine grid, bins the points by a counting sort
+ * over fine-grid bins (cf. Sec. 5.1) and builds the subproblem list (cf. Sec.
+ * 5.2).  The plan keeps the sorted, folded coordinates, so the caller may
+ * free or overwrite x, y, z after the call has completed on the stream.
+ * M = 0 is allowed.  Errors: BAD_ARG (M < 0, NULL with M > 0), TOO_BIG
+ * (M >= 2^31), ALLOC, CUDA.  Out-of-range points are reported later by
+ * nufft_get_status when opts.chkbnds = 1.
+ */
+int nufft_setpts(nufft_plan plan, int64_t M, const void* x, const void* y, const void* z);
+
+/*
+ * Run the ntransf transforms on device arrays c (ntransf * M complex) and f
+ * (ntransf * N_1 ... N_d complex).  Type 1 reads c and writes f (spread,
+ * Eq. (bl); FFT, Eq. (dft1); truncate and correct, Eq. (pb1)).  Type 2 reads
+ * f and writes c (pre-correct and pad, Sec. 3.2 step 1; FFT, Eq. (dft);
+ * interpolate, Eq. (interp)).  With M = 0 a type-1 plan writes f = 0 and a
+ * type-2 plan does nothing.  Errors: BAD_ARG, NOT_SET, CUDA, CUFFT.
+ */
+int nufft_execute(nufft_plan plan, void* c, void* f);
+
+/* Free every resource of the plan (synchronises its stream).  NULL is accepted. */
+int nufft_destroy(nufft_plan plan);
+
+/*
+ * Synchronise the plan's stream and return the first asynchronous error the
+ * device recorded since the last call (NUFFT_ERR_OUT_OF_RANGE, or
+ * NUFFT_ERR_CUDA for a failed launch), then clear it.  NUFFT_OK otherwise.
+ */
+int nufft_get_status(nufft_plan plan);
+
+/*
+ * With opts.debug = 1: synchronise and copy up to n step timings in
+ * milliseconds of the most recent setpts / execute into ms:
+ *   [0] setpts: fold + bin count   [1] setpts: scans + subproblem list
+ *   [2] setpts: scatter            [3] execute: spread or pre-correct/pad
+ *   [4] execute: FFT               [5] execute: deconvolve or interpolate
+ * (for type 2, [3] is pre-correct and [5] interpolation).  Returns the number
+ * of entries written, or a negative error code.
+ */
+int nufft_get_timings(nufft_plan plan, double* ms, int n);
+
+/*
+ * Plan facts, for callers and tests.  Any output pointer may be NULL.
+ * w, beta: kernel width and ES parameter; n: dim fine-grid sizes;
+ * bins: dim bin extents; nsub: number of subproblems of the last setpts
+ * (synchronises the stream).
+ */
+int nufft_plan_info(nufft_plan plan, int* w, double* beta, int64_t* n, int* bins, int64_t* nsub);
+
+/* Static text for a status code. */
+const char* nufft_strerror(int code);
+
+/* ------------------------------------------------------------------ host-only
+ * The following run on the host only (no device call), so they work without
+ * a GPU.  They expose the plan's parameter rules and correction factors.
+ */
+
+/*
+ * Parameters of Eq. (params) and Sec. 3.1.1 for tolerance eps:
+ * *w, *beta, and n[0..dim-1] from nmodes[0..dim-1].  Returns NUFFT_OK,
+ * NUFFT_WARN_EPS_TOO_SMALL, or NUFFT_ERR_BAD_ARG.
+ */
+int nufft_choose_params(int dim, const int64_t* nmodes, double eps, int prec, int* w, double* beta,
+                        int64_t* n);
+
+/*
+ * Correction factors of Eq. (pk1) for one dimension: out[m] = 2 / (w phi^(alpha k)),
+ * k = m - floor(N/2), m = 0..N-1, alpha = pi w / n (Eq. (al)), with phi^ from
+ * the 2p-node Gauss-Legendre rule of Eq. (quad), p = ceil(1.5 w + 2), and the
+ * cosines generated by phase winding (Sec. 3.1.1).  Double precision.
+ * Returns NUFFT_OK or NUFFT_ERR_BAD_ARG.
+ */
+int nufft_correction_factors(int64_t N, int64_t n, int w, double beta, double* out);
+
+/* Smallest 2^a 3^b 5^c >= m (m >= 1); returns -1 on overflow or m < 1. */
+int64_t nufft_next235(int64_t m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFFT_GB300_H */

@@ -1,0 +1,313 @@
+"""CPU oracle for the type-1 / type-2 ES-kernel NUFFT (arXiv:1808.06736).
+
+TEST INFRASTRUCTURE ONLY.  The product path (the CUDA library and its Python
+binding) never imports, loads or calls this package.  Only the tests, the
+smoke check and the CPU-baseline leg of the benchmark use it.  It shares no
+code with the CUDA path; the two meet only through the seeded input
+generators in ``nufft_inputs.py``, which hold none of the method's arithmetic.
+
+Two levels, both in IEEE double precision:
+
+* O1 -- direct evaluation of the exponential sums Eq. (1) (type 1) and
+  Eq. (2) (type 2), in ``nufft_oracle.c``.
+* O2 -- the paper's three-step algorithm written plainly: parameters by
+  Eq. (params) and Sec. 3.1 (fine grid size), spreading Eq. (bl) /
+  interpolation Eq. (interp) as direct loops (C), the n-point DFT Eq. (dft1) /
+  Eq. (dft) with scipy's FFT, and the correction Eq. (pk) with the kernel
+  transform from the Gauss-Legendre rule Eq. (quad).
+
+Readings of the paper that these functions fix (where it is silent or
+inconsistent):
+
+* mode arrays run over increasing k in every dimension, dimension 1 fastest;
+* both types compute sums with exp(+i isign k.x); the type-2 DFT uses the
+  same sign as the transform (Eq. (dft) prints "+", which only holds for
+  isign = +1);
+* w = ceil(log10(1/eps) - 1e-9) + 1, clamped to [2, 16] (the guard keeps
+  eps = 1e-5 at w = 6 against rounding in log10; the clamp is beta <= 36,
+  Sec. 3.3);
+* the w nodes of a coordinate start at ceil(u - w/2), u = x / h;
+* p = ceil(1.5 w + 2) positive Gauss-Legendre nodes (Sec. 3.1.1).
+
+Parity pins for every function live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nufft_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``nufft_oracle.c`` into ``liboracle.so`` with gcc (IEEE math, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int64)
+        i64 = ctypes.c_int64
+        lib.oracle_type1_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ctypes.c_int, i64, ip, dp]
+        lib.oracle_type2_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, ip, dp, ctypes.c_int, dp]
+        lib.oracle_spread.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double, dp]
+        lib.oracle_interp.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double, dp]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the direct sums use."""
+    return int(_L().oracle_num_threads())
+
+
+# ----------------------------------------------------------------- helpers
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _coords(xs):
+    """List of d float64 contiguous coordinate arrays (+ padding for the C ABI)."""
+    xs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in xs]
+    d = len(xs)
+    assert 1 <= d <= 3
+    dummy = np.zeros(1)
+    full = xs + [dummy] * (3 - d)
+    return d, xs, full
+
+
+def _cplx(a) -> np.ndarray:
+    """complex128 contiguous copy viewed as interleaved float64."""
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def mode_range(N: int) -> np.ndarray:
+    """The index set I_N of Sec. 1: -N/2..N/2-1 (N even), -(N-1)/2..(N-1)/2 (N odd)."""
+    return np.arange(N, dtype=np.int64) - (N // 2)
+
+
+def mode_list(Ns) -> np.ndarray:
+    """All k in I_{N_1} x ... x I_{N_d} as an (N, d) int64 array, dimension 1 fastest."""
+    grids = np.meshgrid(*[mode_range(n) for n in reversed(Ns)], indexing="ij")
+    return np.stack([g.ravel() for g in reversed(grids)], axis=1).astype(np.int64)
+
+
+def mode_index(k: np.ndarray, Ns) -> np.ndarray:
+    """Flat position of mode vectors k (m x d) in a mode array (dimension 1 fastest)."""
+    idx = np.zeros(k.shape[0], dtype=np.int64)
+    stride = 1
+    for i, n in enumerate(Ns):
+        idx += (k[:, i] + n // 2) * stride
+        stride *= n
+    return idx
+
+
+def rel_l2(a, b) -> float:
+    """Relative l2 error ||a - b|| / ||b|| (Sec. 4.2's epsilon)."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+
+
+# --------------------------------------------------------------- O1 (truth)
+def direct_type1(xs, c, isign: int, Ns, modes: np.ndarray | None = None) -> np.ndarray:
+    """Eq. (1): f_k = sum_j c_j exp(i isign k.x_j), for all k in I_N or the given (m, d) modes."""
+    d, xs, full = _coords(xs)
+    c = _cplx(c)
+    M = c.shape[0]
+    k = mode_list(Ns) if modes is None else np.ascontiguousarray(modes, dtype=np.int64)
+    assert k.shape[1] == d
+    f = np.zeros(k.shape[0], dtype=np.complex128)
+    _L().oracle_type1_direct(d, M, _dptr(full[0]), _dptr(full[1]), _dptr(full[2]),
+                             _dptr(c.view(np.float64)), int(isign), k.shape[0], _iptr(k),
+                             _dptr(f.view(np.float64)))
+    return f
+
+
+def direct_type2(xs, f, isign: int, Ns) -> np.ndarray:
+    """Eq. (2) with the interface sign: c_j = sum_{k in I_N} f_k exp(i isign k.x_j)."""
+    d, xs, full = _coords(xs)
+    f = _cplx(f).ravel()
+    N = np.ascontiguousarray(Ns, dtype=np.int64)
+    assert f.shape[0] == int(np.prod(N))
+    nt = xs[0].shape[0]
+    c = np.zeros(nt, dtype=np.complex128)
+    _L().oracle_type2_direct(d, nt, _dptr(full[0]), _dptr(full[1]), _dptr(full[2]), _iptr(N),
+                             _dptr(f.view(np.float64)), int(isign), _dptr(c.view(np.float64)))
+    return c
+
+
+# ---------------------------------------------------------- parameters (a0)
+def next235(m: int) -> int:
+    """Smallest integer of the form 2^q 3^p 5^r that is >= m (Sec. 3.1.1)."""
+    m = max(int(m), 1)
+    n = m
+    while True:
+        r = n
+        for p in (2, 3, 5):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return n
+        n += 1
+
+
+def kernel_width(eps: float) -> int:
+    """Eq. (params): w = ceil(log10(1/eps)) + 1, with the guard and clamp read in the module docstring."""
+    w = int(math.ceil(math.log10(1.0 / eps) - 1e-9)) + 1
+    return min(max(w, 2), 16)
+
+
+def es_beta(w: int) -> float:
+    """Eq. (params): beta = 2.30 w (sigma = 2)."""
+    return 2.30 * w
+
+
+def fine_grid_size(N: int, w: int, sigma: float = 2.0) -> int:
+    """Sec. 3.1.1: smallest 2^q 3^p 5^r not less than sigma N nor 2w."""
+    return next235(max(int(math.ceil(sigma * N)), 2 * w))
+
+
+def choose_params(eps: float, Ns):
+    """(w, beta, [n_1..n_d]) for tolerance eps and mode counts Ns (Sec. 3, Eq. (params))."""
+    w = kernel_width(eps)
+    return w, es_beta(w), [fine_grid_size(n, w) for n in Ns]
+
+
+# --------------------------------------------------- kernel and its transform
+def es_kernel(z, beta: float):
+    """Eq. (ES): exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, zero outside."""
+    z = np.asarray(z, dtype=np.float64)
+    out = np.zeros_like(z)
+    m = np.abs(z) <= 1.0
+    out[m] = np.exp(beta * (np.sqrt(1.0 - z[m] ** 2) - 1.0))
+    return out
+
+
+def gl_quadrature_nodes(w: int):
+    """Positive nodes and weights of the 2p-point Gauss-Legendre rule, p = ceil(1.5 w + 2) (Sec. 3.1.1)."""
+    p = int(math.ceil(1.5 * w + 2))
+    q, wq = np.polynomial.legendre.leggauss(2 * p)
+    keep = q > 0
+    return q[keep], wq[keep]
+
+
+def kernel_ft(xi, w: int, beta: float, kernel=None):
+    """phi^(xi) = int_{-1}^{1} phi(z) e^{i xi z} dz by Eq. (quad)'s rule: 2 sum_j w_j phi(q_j) cos(xi q_j).
+
+    ``kernel`` (a function of z) replaces the ES kernel, which lets the tests
+    push a kernel with a known transform through the same rule.
+    """
+    q, wq = gl_quadrature_nodes(w)
+    phi = es_kernel(q, beta) if kernel is None else kernel(q)
+    xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+    return 2.0 * (np.cos(np.outer(xi, q)) @ (wq * phi))
+
+
+def correction_factors(N: int, n: int, w: int, beta: float) -> np.ndarray:
+    """Eq. (pk1): p_k = h / psi^(k) = 2 / (w phi^(alpha k)), alpha = pi w / n (Eq. (al)), k in I_N."""
+    alpha = math.pi * w / n
+    return 2.0 / (w * kernel_ft(alpha * mode_range(N), w, beta))
+
+
+# ------------------------------------------------------------- O2 pieces
+def spread(xs, c, ns, w: int, beta: float) -> np.ndarray:
+    """Eq. (bl): fine-grid values b_l (complex, shape (n_d, ..., n_1))."""
+    d, xs, full = _coords(xs)
+    c = _cplx(c)
+    n = np.ascontiguousarray(ns, dtype=np.int64)
+    b = np.zeros(int(np.prod(n)), dtype=np.complex128)
+    _L().oracle_spread(d, c.shape[0], _dptr(full[0]), _dptr(full[1]), _dptr(full[2]),
+                       _dptr(c.view(np.float64)), _iptr(n), int(w), float(beta),
+                       _dptr(b.view(np.float64)))
+    return b.reshape(tuple(reversed([int(v) for v in ns])))
+
+
+def interp(xs, b, ns, w: int, beta: float) -> np.ndarray:
+    """Eq. (interp): c_j = sum_l b_l psi~(l h - x_j)."""
+    d, xs, full = _coords(xs)
+    b = _cplx(b).ravel()
+    n = np.ascontiguousarray(ns, dtype=np.int64)
+    M = xs[0].shape[0]
+    c = np.zeros(M, dtype=np.complex128)
+    _L().oracle_interp(d, M, _dptr(full[0]), _dptr(full[1]), _dptr(full[2]),
+                       _dptr(b.view(np.float64)), _iptr(n), int(w), float(beta),
+                       _dptr(c.view(np.float64)))
+    return c
+
+
+def _workers() -> int:
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+def dft(b: np.ndarray, isign: int) -> np.ndarray:
+    """Eq. (dft1) / Eq. (dft): sum_l exp(isign 2 pi i l.k / n) b_l over all axes (unnormalised)."""
+    import scipy.fft as sfft
+    if isign > 0:
+        return sfft.ifftn(b, norm="forward", workers=_workers())
+    return sfft.fftn(b, workers=_workers())
+
+
+def _truncation_index(Ns, ns):
+    """Fine-grid positions k mod n of the modes k in I_N, per axis in array order (slowest first)."""
+    return np.ix_(*[np.mod(mode_range(N), n) for N, n in zip(reversed(Ns), reversed(ns))])
+
+
+def _outer_correction(Ns, ns, w, beta):
+    """Eq. (pk): the separable p_k as an array of shape (N_d, ..., N_1)."""
+    p = None
+    for N, n in zip(reversed(Ns), reversed(ns)):
+        pk = correction_factors(N, n, w, beta)
+        p = pk if p is None else np.multiply.outer(p, pk)
+    return p
+
+
+def type1(xs, c, isign: int, Ns, eps: float | None = None, w: int | None = None,
+          beta: float | None = None, ns=None) -> np.ndarray:
+    """O2 type 1 (Sec. 3.1): spread Eq. (bl), DFT Eq. (dft1) with sign isign, truncate and
+    correct Eq. (pb1)/(pk).  Parameters from eps unless (w, beta, ns) are given."""
+    Ns = [int(v) for v in Ns]
+    if w is None:
+        w, beta, ns = choose_params(eps, Ns)
+    b = spread(xs, c, ns, w, beta)
+    bh = dft(b, isign)
+    f = bh[_truncation_index(Ns, ns)] * _outer_correction(Ns, ns, w, beta)
+    return f.ravel()
+
+
+def type2(xs, f, isign: int, Ns, eps: float | None = None, w: int | None = None,
+          beta: float | None = None, ns=None) -> np.ndarray:
+    """O2 type 2 (Sec. 3.2): pre-correct and zero-pad, DFT Eq. (dft) with sign isign,
+    interpolate Eq. (interp)."""
+    Ns = [int(v) for v in Ns]
+    if w is None:
+        w, beta, ns = choose_params(eps, Ns)
+    f = _cplx(f).reshape(tuple(reversed(Ns)))
+    bh = np.zeros(tuple(reversed([int(v) for v in ns])), dtype=np.complex128)
+    bh[_truncation_index(Ns, ns)] = f * _outer_correction(Ns, ns, w, beta)
+    b = dft(bh, isign)
+    return interp(xs, b, ns, w, beta)

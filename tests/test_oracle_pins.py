@@ -1,0 +1,325 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every check compares the oracle with something other than itself: numpy's
+FFT (the uniform-point special case of Eq. (1)), scipy's adaptive quadrature
+and the Kaiser-Bessel closed form Eq. (KBhat) (for the Gauss-Legendre rule of
+Eq. (quad)), the asymptotic form Eq. (EShat1), values the paper prints
+(tests/golden/paper_parameters.txt), the exact adjoint relation of Sec. 4.1,
+the heuristic error level of Remark r:heur, and brute force on tiny inputs.
+The last tests plant mistakes in the oracle and check the pins catch them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import nufft_inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.txt")
+
+
+def _golden():
+    rows = []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append(line.split())
+    return rows
+
+
+def _es_ft_adaptive(beta, xi):
+    """phi^(xi) by scipy's adaptive quadrature (independent of the GL rule)."""
+    f = lambda z: math.exp(beta * (math.sqrt(max(1.0 - z * z, 0.0)) - 1.0)) * math.cos(xi * z)
+    return 2.0 * integrate.quad(f, 0.0, 1.0, epsabs=0.0, epsrel=1e-12, limit=800)[0]
+
+
+# ------------------------------------------------------------ parameters
+def test_width_golden(oracle_mod):
+    rows = [r for r in _golden() if r[0] == "width"]
+    assert len(rows) == 3
+    for _, eps, w, *_ in rows:
+        assert oracle_mod.kernel_width(float(eps)) == int(w), (eps, w)
+
+
+def test_beta_golden(oracle_mod):
+    (row,) = [r for r in _golden() if r[0] == "beta_w"]
+    w, beta = int(row[1]), float(row[2])
+    assert abs(oracle_mod.es_beta(w) - beta) < 0.5
+
+
+def test_gamma_golden(oracle_mod):
+    # Eq. (gam): beta = gamma pi w (1 - 1/(2 sigma)), sigma = 2
+    for row in [r for r in _golden() if r[0] == "gamma"]:
+        factor, gamma = float(row[1]), float(row[2])
+        assert abs(factor / (math.pi * (1 - 1 / 4.0)) - gamma) < 1e-3
+    # the oracle's beta/w is the 2.30 factor
+    assert oracle_mod.es_beta(10) / 10 == pytest.approx(2.30)
+
+
+def test_grid_golden(oracle_mod):
+    (row,) = [r for r in _golden() if r[0] == "grid"]
+    N, w, n = int(row[1]), int(row[2]), int(row[3])
+    assert oracle_mod.fine_grid_size(N, w) == n
+
+
+def test_next235_against_enumeration(oracle_mod):
+    # all 2^a 3^b 5^c up to 5000, built by products (not by factoring)
+    vals = sorted({2 ** a * 3 ** b * 5 ** c for a in range(13) for b in range(9) for c in range(7)
+                   if 2 ** a * 3 ** b * 5 ** c <= 5000})
+    for m in list(range(1, 700)) + [999, 1000, 1001, 2047, 2049, 4000]:
+        expect = min(v for v in vals if v >= m)
+        assert oracle_mod.next235(m) == expect, m
+
+
+def test_eps_guard(oracle_mod):
+    # A4 reading: rounding in log10 must not push eps = 1e-k to the next width
+    for k in range(1, 15):
+        assert oracle_mod.kernel_width(10.0 ** (-k)) == min(k + 1, 16)
+    assert oracle_mod.kernel_width(0.99e-5) == 7
+    assert oracle_mod.kernel_width(1e-20) == 16
+    assert oracle_mod.kernel_width(0.5) == 2
+
+
+# --------------------------------------------------- kernel transform
+@pytest.mark.parametrize("w", [2, 3, 4, 5, 6, 7, 8, 10, 13, 16])
+def test_kernel_ft_vs_adaptive_quadrature(oracle_mod, w):
+    """Sec. 3.1.1: p >= 1.5 w + 2 nodes give errors below eps = 10^-(w-1) for |k| <= N/2."""
+    beta = oracle_mod.es_beta(w)
+    xi = np.linspace(0.0, math.pi * w / 4.0, 7)  # alpha k for |k| <= N/2 with n = 2N
+    gl = oracle_mod.kernel_ft(xi, w, beta)
+    ref = np.array([_es_ft_adaptive(beta, v) for v in xi])
+    err = np.max(np.abs(gl - ref) / np.abs(ref))
+    assert err < max(10.0 ** (-(w - 1)), 1e-14), err  # 1e-14: double rounding floor
+
+
+@pytest.mark.parametrize("w", [4, 6, 10, 16])
+def test_kernel_ft_rule_on_kaiser_bessel(oracle_mod, w):
+    """The same rule applied to the KB kernel Eq. (KB) reproduces its closed form Eq. (KBhat)."""
+    beta = oracle_mod.es_beta(w)
+    kb = lambda z: special.i0(beta * np.sqrt(np.maximum(1.0 - z * z, 0.0))) / special.i0(beta)
+    xi = np.linspace(0.0, math.pi * w / 4.0, 9)  # the range |k| <= N/2 needs
+    s = np.sqrt(beta ** 2 - xi ** 2)
+    closed = 2.0 / special.i0(beta) * np.sinh(s) / s
+    got = oracle_mod.kernel_ft(xi, w, beta, kernel=kb)
+    assert np.max(np.abs(got - closed) / closed) < 1e-10
+
+
+@pytest.mark.parametrize("w", [4, 8, 12, 16])
+def test_kernel_ft_asymptotic(oracle_mod, w):
+    """Eq. (EShat1): phi^(rho beta) ~ sqrt(2 pi / beta) (1 - rho^2)^(-3/4) e^{beta (sqrt(1-rho^2) - 1)} [1 + O(1/beta)]."""
+    beta = oracle_mod.es_beta(w)
+    for rho in (0.0, 0.3, 0.6):
+        got = oracle_mod.kernel_ft([rho * beta], w, beta)[0]
+        asy = math.sqrt(2 * math.pi / beta) * (1 - rho ** 2) ** -0.75 * math.exp(beta * (math.sqrt(1 - rho ** 2) - 1))
+        rel = abs(got - asy) / got
+        assert rel * beta < 1.0, (rho, rel)
+        assert rel * beta > 0.1  # the O(1/beta) term is really there (not an accidental match)
+
+
+def test_correction_factor_definition(oracle_mod):
+    """Eq. (pk1): p_k = h / psi^(k), with psi^(k) = alpha phi^(alpha k) and phi^ from adaptive quadrature."""
+    N, n, w = 40, 80, 6
+    beta = oracle_mod.es_beta(w)
+    p = oracle_mod.correction_factors(N, n, w, beta)
+    h, alpha = 2 * math.pi / n, math.pi * w / n
+    for m in (0, 7, 20, 39):
+        k = m - N // 2
+        ref = h / (alpha * _es_ft_adaptive(beta, alpha * k))
+        assert p[m] == pytest.approx(ref, rel=1e-8)
+
+
+# -------------------------------------------------------- O1 direct sums
+@pytest.mark.parametrize("N", [16, 15])
+@pytest.mark.parametrize("isign", [1, -1])
+def test_direct_type1_is_dft_on_uniform_points(oracle_mod, N, isign):
+    """Sec. 1: with x_j = 2 pi j / M and M = N, Eq. (1) is a DFT."""
+    x = 2 * math.pi * np.arange(N) / N
+    c = I.complex_normal(11, N)
+    f = oracle_mod.direct_type1([x], c, isign, [N])
+    ref = np.fft.ifft(c) * N if isign > 0 else np.fft.fft(c)
+    k = oracle_mod.mode_range(N)
+    np.testing.assert_allclose(f, ref[np.mod(k, N)], rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("isign", [1, -1])
+def test_direct_type2_is_dft_on_uniform_points_2d(oracle_mod, isign):
+    """Eq. (2) on a tensor grid of points equals a 2D DFT; N1 != N2 catches transposed axes."""
+    N1, N2 = 8, 5
+    j1, j2 = np.meshgrid(np.arange(N1), np.arange(N2), indexing="xy")
+    x = (2 * math.pi * j1 / N1).ravel()
+    y = (2 * math.pi * j2 / N2).ravel()
+    f = I.complex_normal(12, N1 * N2)
+    c = oracle_mod.direct_type2([x, y], f, isign, [N1, N2])
+    # place f (k1 fastest, increasing k) into FFT order, axes (k2, k1)
+    F = np.zeros((N2, N1), dtype=complex)
+    K1, K2 = np.meshgrid(oracle_mod.mode_range(N1), oracle_mod.mode_range(N2), indexing="xy")
+    F[np.mod(K2, N2), np.mod(K1, N1)] = f.reshape(N2, N1)
+    ref = np.fft.ifft2(F) * (N1 * N2) if isign > 0 else np.fft.fft2(F)
+    np.testing.assert_allclose(c, ref.ravel(), rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_direct_type1_3d_matches_fftn(oracle_mod):
+    N = (4, 6, 5)
+    g = np.meshgrid(*[np.arange(n) for n in reversed(N)], indexing="ij")
+    xs = [(2 * math.pi * g[2 - i] / N[i]).ravel() for i in range(3)]
+    c = I.complex_normal(13, int(np.prod(N)))
+    f = oracle_mod.direct_type1(xs, c, -1, list(N))
+    C = c.reshape(tuple(reversed(N)))
+    ref = np.fft.fftn(C)
+    idx = np.ix_(*[np.mod(oracle_mod.mode_range(n), n) for n in reversed(N)])
+    np.testing.assert_allclose(f, ref[idx].ravel(), rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_direct_adjoint(oracle_mod):
+    """Sec. 1: type 2 with sign -s is the adjoint of type 1 with sign s."""
+    N = [5, 4, 3]
+    xs = I.points(21, 17, 3)
+    c = I.complex_normal(22, 17)
+    f = I.complex_normal(23, 60)
+    a = np.vdot(f, oracle_mod.direct_type1(xs, c, 1, N))
+    b = np.vdot(oracle_mod.direct_type2(xs, f, -1, N), c)
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_direct_type1_mode_subset(oracle_mod):
+    N = [6, 5]
+    xs = I.points(24, 30, 2)
+    c = I.complex_normal(25, 30)
+    full = oracle_mod.direct_type1(xs, c, 1, N)
+    k = np.array([[-3, -2], [2, 2], [0, 0], [1, -1]])
+    sub = oracle_mod.direct_type1(xs, c, 1, N, modes=k)
+    np.testing.assert_allclose(sub, full[oracle_mod.mode_index(k, N)], rtol=1e-13, atol=1e-13)
+
+
+def test_direct_large_point_split_path(oracle_mod):
+    """The few-modes / many-points branch of the type-1 sum agrees with the per-mode branch."""
+    xs = I.points(26, 20000, 3)
+    c = I.complex_normal(27, 20000)
+    k = np.array([[1, 2, 3], [-4, 0, 5]])
+    a = oracle_mod.direct_type1(xs, c, 1, [8, 8, 12], modes=k)
+    ph = np.outer(k[:, 0], xs[0]) + np.outer(k[:, 1], xs[1]) + np.outer(k[:, 2], xs[2])
+    b = np.exp(1j * ph) @ c
+    np.testing.assert_allclose(a, b, rtol=1e-11)
+
+
+# ----------------------------------------------------------- O2 algorithm
+CASES = [(1, [100], 300), (2, [24, 17], 400), (3, [12, 10, 9], 500)]
+
+
+def _heuristic_eps_inf(oracle_mod, eps, Ns):
+    """Remark r:heur: eps_inf ~ |psi^(n - N/2) / psi^(N/2)|, worst dimension (adaptive quadrature)."""
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    out = 0.0
+    for N, n in zip(Ns, ns):
+        a = math.pi * w / n
+        out = max(out, abs(_es_ft_adaptive(beta, a * (n - N / 2)) / _es_ft_adaptive(beta, a * N / 2)))
+    return out
+
+
+@pytest.mark.parametrize("d,Ns,M", CASES)
+@pytest.mark.parametrize("eps", [1e-3, 1e-5, 1e-9, 1e-12])
+def test_o2_error_vs_truth(oracle_mod, d, Ns, M, eps):
+    """Sec. 4.2: relative l2 error of the ES NUFFT tracks eps; within 10 eps and within the
+    heuristic level eps_inf of Remark r:heur (between eps_inf/20 and 1.5 eps_inf)."""
+    xs = I.points(1, M, d)
+    c = I.complex_normal(2, M)
+    f = I.complex_normal(3, int(np.prod(Ns)))
+    heur = _heuristic_eps_inf(oracle_mod, eps, Ns)
+    e1 = oracle_mod.rel_l2(oracle_mod.type1(xs, c, 1, Ns, eps=eps), oracle_mod.direct_type1(xs, c, 1, Ns))
+    e2 = oracle_mod.rel_l2(oracle_mod.type2(xs, f, -1, Ns, eps=eps), oracle_mod.direct_type2(xs, f, -1, Ns))
+    for e in (e1, e2):
+        assert e <= 10 * eps
+        assert heur / 20 < e < 1.5 * heur, (e, heur)
+
+
+@pytest.mark.parametrize("d,Ns,M", CASES)
+@pytest.mark.parametrize("isign", [1, -1])
+def test_o2_adjoint_to_rounding(oracle_mod, d, Ns, M, isign):
+    """Sec. 4.1: the discrete type-2 algorithm is the exact adjoint of the type-1 algorithm."""
+    xs = I.points(4, M, d)
+    c = I.complex_normal(5, M)
+    f = I.complex_normal(6, int(np.prod(Ns)))
+    w, beta, ns = oracle_mod.choose_params(1e-6, Ns)
+    F1c = oracle_mod.type1(xs, c, isign, Ns, w=w, beta=beta, ns=ns)
+    F2f = oracle_mod.type2(xs, f, -isign, Ns, w=w, beta=beta, ns=ns)
+    a, b = np.vdot(f, F1c), np.vdot(F2f, c)
+    assert abs(a - b) < 1e-12 * np.linalg.norm(f) * np.linalg.norm(F1c)
+
+
+def test_o2_single_point(oracle_mod):
+    """M = 1, c = 1: Eq. (1) gives f_k = exp(i k.x0); x0 = 0 gives f = 1."""
+    Ns = [9, 8]
+    for x0 in ([0.0, 0.0], [1.1, -2.7]):
+        f = oracle_mod.type1([[x0[0]], [x0[1]]], [1.0 + 0j], 1, Ns, eps=1e-9)
+        k = oracle_mod.mode_list(Ns)
+        ref = np.exp(1j * (k[:, 0] * x0[0] + k[:, 1] * x0[1]))
+        assert np.max(np.abs(f - ref)) < 1e-8
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("eps", [1e-4, 1e-10])
+def test_o2_brute_force_tiny_with_edge_points(oracle_mod, d, eps):
+    """N_i <= 8, M <= 12 with points on grid nodes, at -pi, just below pi and outside [-pi, pi)."""
+    Ns = [8, 7, 6][:d]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    xs, M = I.edge_points(d, ns)
+    c = I.complex_normal(7, M)
+    f = I.complex_normal(8, int(np.prod(Ns)))
+    e1 = oracle_mod.rel_l2(oracle_mod.type1(xs, c, 1, Ns, eps=eps), oracle_mod.direct_type1(xs, c, 1, Ns))
+    e2 = oracle_mod.rel_l2(oracle_mod.type2(xs, f, -1, Ns, eps=eps), oracle_mod.direct_type2(xs, f, -1, Ns))
+    assert e1 <= 10 * eps and e2 <= 10 * eps, (e1, e2)
+
+
+def test_o2_periodicity(oracle_mod):
+    """Eq. (ppsi1): shifting every point by 2 pi leaves the transforms unchanged."""
+    xs = I.points(9, 50, 2)
+    c = I.complex_normal(10, 50)
+    a = oracle_mod.type1(xs, c, 1, [10, 12], eps=1e-8)
+    b = oracle_mod.type1([xs[0] + 2 * math.pi, xs[1] - 2 * math.pi], c, 1, [10, 12], eps=1e-8)
+    assert oracle_mod.rel_l2(a, b) < 1e-12
+
+
+# -------------------------------------------------- planted mistakes
+def _err_t1(oracle_mod, Ns=(12, 10, 9), eps=1e-6):
+    xs = I.points(31, 200, len(Ns))
+    c = I.complex_normal(32, 200)
+    return oracle_mod.rel_l2(oracle_mod.type1(xs, c, 1, list(Ns), eps=eps),
+                             oracle_mod.direct_type1(xs, c, 1, list(Ns)))
+
+
+def test_planted_mistakes_are_caught(oracle_mod, monkeypatch):
+    base = _err_t1(oracle_mod)
+    assert base < 1e-5
+    # (a) a dropped factor 2/w in Eq. (pk1)
+    orig_cf = oracle_mod.correction_factors
+    monkeypatch.setattr(oracle_mod, "correction_factors", lambda N, n, w, b: orig_cf(N, n, w, b) * w / 2)
+    assert _err_t1(oracle_mod) > 1e-1
+    monkeypatch.setattr(oracle_mod, "correction_factors", orig_cf)
+    # (b) the wrong DFT sign
+    orig_dft = oracle_mod.dft
+    monkeypatch.setattr(oracle_mod, "dft", lambda b, s: orig_dft(b, -s))
+    assert _err_t1(oracle_mod) > 1e-1
+    monkeypatch.setattr(oracle_mod, "dft", orig_dft)
+    # (c) beta off by 10 percent (a mis-typed 2.30)
+    orig_beta = oracle_mod.es_beta
+    monkeypatch.setattr(oracle_mod, "es_beta", lambda w: 2.07 * w)
+    assert _err_t1(oracle_mod) > 2 * base  # and test_beta_golden fails too
+    monkeypatch.setattr(oracle_mod, "es_beta", orig_beta)
+    # (d) each dimension's correction computed with another dimension's fine-grid size
+    orig_outer = oracle_mod._outer_correction
+    monkeypatch.setattr(oracle_mod, "_outer_correction",
+                        lambda Ns, ns, w, b: orig_outer(Ns, list(ns)[::-1], w, b))
+    assert _err_t1(oracle_mod) > 1e-3
+    monkeypatch.setattr(oracle_mod, "_outer_correction", orig_outer)
+    # (e) the nodes of a coordinate starting one cell late (ceil(u - w/2) + 1)
+    orig_spread = oracle_mod.spread
+    monkeypatch.setattr(oracle_mod, "spread",
+                        lambda xs, c, ns, w, b: orig_spread([np.asarray(v) - 2 * math.pi / n for v, n in zip(xs, ns)],
+                                                            c, ns, w, b))
+    assert _err_t1(oracle_mod) > 1e-1
+    monkeypatch.setattr(oracle_mod, "spread", orig_spread)
+    assert _err_t1(oracle_mod) == pytest.approx(base)
