@@ -1,0 +1,277 @@
+"""GB300 (sm_103a) type-1 / type-2 NUFFT with the "exponential of semicircle" kernel
+(Barnett, Magland & af Klinteberg, arXiv:1808.06736).
+
+Python binding of ``libnufft_gb300.so`` (C ABI: include/nufft_gb300.h).  The
+module-level ``nufft_*`` functions carry the C names and only marshal
+arguments; ``Plan`` adds torch-tensor handling (device memory, the current
+CUDA stream, host <-> device copies for CPU tensors).  Every step of a
+transform runs in the library's CUDA kernels and cuFFT; there is no CPU
+fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
+    "nufft_execute", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
+    "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235", "library_path",
+    "NUFFT_C64", "NUFFT_C128",
+]
+
+NUFFT_C64 = 1
+NUFFT_C128 = 2
+STATUS = {
+    0: "NUFFT_OK", 1: "NUFFT_WARN_EPS_TOO_SMALL", -1: "NUFFT_ERR_BAD_ARG", -2: "NUFFT_ERR_OUT_OF_RANGE",
+    -3: "NUFFT_ERR_ALLOC", -4: "NUFFT_ERR_CUDA", -5: "NUFFT_ERR_CUFFT", -6: "NUFFT_ERR_NOT_SET",
+    -7: "NUFFT_ERR_TOO_BIG",
+}
+
+
+class NufftError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, STATUS.get(code, "unknown"), code))
+
+
+class nufft_opts(ctypes.Structure):
+    _fields_ = [("debug", ctypes.c_int), ("chkbnds", ctypes.c_int), ("modeord", ctypes.c_int),
+                ("bin_size", ctypes.c_int * 3), ("max_subprob", ctypes.c_int), ("threads", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("libnufft_gb300.so is not built (expected at %s); run "
+                          "paper_1808_06736_gb300.build.build() or __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    pi64 = ctypes.POINTER(ctypes.c_int64)
+    lib.nufft_default_opts.argtypes = [ctypes.POINTER(nufft_opts)]
+    lib.nufft_makeplan.argtypes = [i32, i32, pi64, i32, i32, dbl, i32, vp, ctypes.POINTER(nufft_opts),
+                                   ctypes.POINTER(vp)]
+    lib.nufft_setpts.argtypes = [vp, i64, vp, vp, vp]
+    lib.nufft_execute.argtypes = [vp, vp, vp]
+    lib.nufft_destroy.argtypes = [vp]
+    lib.nufft_get_status.argtypes = [vp]
+    lib.nufft_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
+    lib.nufft_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(dbl), pi64, ctypes.POINTER(i32), pi64]
+    lib.nufft_strerror.argtypes = [i32]
+    lib.nufft_strerror.restype = ctypes.c_char_p
+    lib.nufft_choose_params.argtypes = [i32, pi64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), pi64]
+    lib.nufft_correction_factors.argtypes = [i64, i64, i32, dbl, ctypes.POINTER(ctypes.c_double)]
+    lib.nufft_next235.argtypes = [i64]
+    lib.nufft_next235.restype = i64
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------ C-name wrappers
+def nufft_default_opts() -> nufft_opts:
+    o = nufft_opts()
+    _L().nufft_default_opts(ctypes.byref(o))
+    return o
+
+
+def nufft_makeplan(type_: int, dim: int, nmodes, isign: int, ntransf: int, eps: float, prec: int,
+                   stream: int | None, opts: nufft_opts | None):
+    """Returns (status, plan handle)."""
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in nmodes] + [1] * (3 - len(nmodes))))
+    h = ctypes.c_void_p()
+    st = _L().nufft_makeplan(int(type_), int(dim), arr, int(isign), int(ntransf), float(eps), int(prec),
+                             ctypes.c_void_p(stream or 0), ctypes.byref(opts) if opts is not None else None,
+                             ctypes.byref(h))
+    return st, h
+
+
+def nufft_setpts(plan, M: int, x: int, y: int, z: int) -> int:
+    return _L().nufft_setpts(plan, int(M), ctypes.c_void_p(x or 0), ctypes.c_void_p(y or 0), ctypes.c_void_p(z or 0))
+
+
+def nufft_execute(plan, c: int, f: int) -> int:
+    return _L().nufft_execute(plan, ctypes.c_void_p(c or 0), ctypes.c_void_p(f or 0))
+
+
+def nufft_destroy(plan) -> int:
+    return _L().nufft_destroy(plan)
+
+
+def nufft_get_status(plan) -> int:
+    return _L().nufft_get_status(plan)
+
+
+def nufft_get_timings(plan, n: int = 6):
+    buf = (ctypes.c_double * n)()
+    k = _L().nufft_get_timings(plan, buf, n)
+    return k, list(buf)[: max(k, 0)]
+
+
+def nufft_plan_info(plan, dim: int):
+    w, beta = ctypes.c_int(), ctypes.c_double()
+    n = (ctypes.c_int64 * 3)()
+    bins = (ctypes.c_int * 3)()
+    nsub = ctypes.c_int64()
+    st = _L().nufft_plan_info(plan, ctypes.byref(w), ctypes.byref(beta), n, bins, ctypes.byref(nsub))
+    return st, dict(w=w.value, beta=beta.value, n=list(n)[:dim], bins=list(bins)[:dim], nsub=nsub.value)
+
+
+def nufft_strerror(code: int) -> str:
+    return _L().nufft_strerror(int(code)).decode()
+
+
+def nufft_choose_params(dim: int, nmodes, eps: float, prec: int = NUFFT_C128):
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in nmodes] + [1] * (3 - len(nmodes))))
+    w, beta = ctypes.c_int(), ctypes.c_double()
+    n = (ctypes.c_int64 * 3)()
+    st = _L().nufft_choose_params(int(dim), arr, float(eps), int(prec), ctypes.byref(w), ctypes.byref(beta), n)
+    return st, w.value, beta.value, list(n)[:dim]
+
+
+def nufft_correction_factors(N: int, n: int, w: int, beta: float):
+    out = (ctypes.c_double * int(N))()
+    st = _L().nufft_correction_factors(int(N), int(n), int(w), float(beta), out)
+    return st, list(out)
+
+
+def nufft_next235(m: int) -> int:
+    return int(_L().nufft_next235(int(m)))
+
+
+# --------------------------------------------------------------- torch layer
+class Plan:
+    """A type-1 or type-2 plan on one CUDA device, driven with torch tensors.
+
+    type 1: ``execute(c)`` with c of shape (M,) or (ntransf, M) returns f of
+    shape (ntransf, N_d, ..., N_1) (dimension 1 fastest).  type 2:
+    ``execute(f)`` returns c of shape (ntransf, M).  CPU tensors are copied to
+    the device and the result copied back (the end-to-end path).
+    """
+
+    def __init__(self, nufft_type: int, n_modes, eps: float = 1e-6, isign: int | None = None,
+                 n_trans: int = 1, dtype=None, device=None, stream=None, **opts):
+        import torch
+        self._torch = torch
+        self.type = int(nufft_type)
+        self.n_modes = tuple(int(v) for v in n_modes)
+        self.dim = len(self.n_modes)
+        self.isign = int(isign) if isign is not None else (1 if self.type == 1 else -1)
+        self.n_trans = int(n_trans)
+        self.dtype = dtype if dtype is not None else torch.complex64
+        if self.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("dtype must be complex64 or complex128")
+        self.real_dtype = torch.float32 if self.dtype == torch.complex64 else torch.float64
+        self.prec = NUFFT_C64 if self.dtype == torch.complex64 else NUFFT_C128
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("Plan needs a CUDA device")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            o = nufft_default_opts()
+            for k, v in opts.items():
+                if k == "bin_size":
+                    for i, b in enumerate(v):
+                        o.bin_size[i] = int(b)
+                else:
+                    setattr(o, k, int(v))
+            self._h = None
+            st, h = nufft_makeplan(self.type, self.dim, self.n_modes, self.isign, self.n_trans, eps, self.prec,
+                                   self.stream.cuda_stream, o)
+            if st < 0:
+                raise NufftError(st, "nufft_makeplan")
+            self.warning = st
+            self._h = h
+        self.M = None
+        self._keep = ()
+        st, self.info = nufft_plan_info(self._h, self.dim)
+
+    # -- points
+    def setpts(self, x, y=None, z=None):
+        torch = self._torch
+        coords = [x, y, z][: self.dim]
+        if any(v is None for v in coords):
+            raise ValueError("need %d coordinate arrays" % self.dim)
+        dev = []
+        for v in coords:
+            v = torch.as_tensor(v)
+            v = v.to(device=self.device, dtype=self.real_dtype, non_blocking=True).contiguous()
+            dev.append(v)
+        M = dev[0].numel()
+        if any(v.numel() != M for v in dev):
+            raise ValueError("coordinate arrays differ in length")
+        ptrs = [v.data_ptr() for v in dev] + [0] * (3 - self.dim)
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft_setpts(self._h, M, *ptrs)
+        if st < 0:
+            raise NufftError(st, "nufft_setpts")
+        self.M = M
+        self._keep = tuple(dev)
+        return self
+
+    # -- transform
+    def execute(self, data, out=None):
+        torch = self._torch
+        if self.M is None:
+            raise NufftError(-6, "Plan.execute")
+        host = isinstance(data, torch.Tensor) and data.device.type == "cpu"
+        d = torch.as_tensor(data).to(device=self.device, dtype=self.dtype, non_blocking=True).contiguous()
+        nt = self.n_trans
+        Nt = 1
+        for v in self.n_modes:
+            Nt *= v
+        if self.type == 1:
+            if d.numel() != nt * self.M:
+                raise ValueError("expected %d strengths" % (nt * self.M))
+            shape = (nt,) + tuple(reversed(self.n_modes))
+            res = out if out is not None else torch.empty(shape, dtype=self.dtype, device=self.device)
+            c_ptr, f_ptr = d.data_ptr(), res.data_ptr()
+        else:
+            if d.numel() != nt * Nt:
+                raise ValueError("expected %d coefficients" % (nt * Nt))
+            res = out if out is not None else torch.empty((nt, self.M), dtype=self.dtype, device=self.device)
+            c_ptr, f_ptr = res.data_ptr(), d.data_ptr()
+        if not res.is_contiguous() or res.device != self.device or res.dtype != self.dtype:
+            raise ValueError("out must be a contiguous %s tensor on %s" % (self.dtype, self.device))
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft_execute(self._h, c_ptr, f_ptr)
+        if st < 0:
+            raise NufftError(st, "nufft_execute")
+        self._keep_exec = (d,)
+        if host:
+            return res.to("cpu")
+        return res
+
+    def status(self) -> int:
+        return nufft_get_status(self._h)
+
+    def timings(self):
+        return nufft_get_timings(self._h)[1]
+
+    def nsub(self) -> int:
+        return nufft_plan_info(self._h, self.dim)[1]["nsub"]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            nufft_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,271 @@
+// setpts: fold the points onto the fine grid and bin them by a counting sort.
+//
+// The paper sorts points into boxes of fine-grid cells before spreading or
+// interpolating, with an "incomplete" histogram sort: count per box, prefix
+// sum into breakpoints, write each point into its box, no order inside a box
+// (Sec. 5.1).  Sorted points are then grouped into subproblems of bounded
+// size (Sec. 5.2).  Here:
+//   k_fold_count  per point: fold, bin id, rank in its bin (global atomicAdd)
+//   k_scan        one block: bin breakpoints + subproblem breakpoints
+//   k_sublist     per bin: its subproblems (bin, first record, count)
+//   k_scatter     per point: folded coordinates relative to the bin origin,
+//                 written as one record at breakpoint + rank
+#include <cmath>
+
+#include "nufft_internal.cuh"
+
+namespace nufft {
+
+FoldConst make_fold_const(const Geom& g) {
+  FoldConst f;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < 3; ++i) {
+    double s = (double)g.n[i] / two_pi;
+    f.s[i] = s;
+    f.s_hi[i] = (float)s;
+    f.s_lo[i] = (float)(s - (double)f.s_hi[i]);
+  }
+  return f;
+}
+
+namespace {
+
+constexpr double kThreePi = 9.424777960769379715387930149839;
+
+// i mod n for the cell index of a folded point; one add or subtract covers
+// every |x| <= 3 pi, the general remainder only runs for points further out.
+__device__ __forceinline__ int wrap_cell(long long i, int n) {
+  if (i < 0) i += n;
+  if (i >= n) i -= n;
+  if ((unsigned long long)i >= (unsigned long long)n) {
+    i %= n;
+    if (i < 0) i += n;
+  }
+  return (int)i;
+}
+
+// u = x n / (2 pi) split as (cell in [0, n), frac in [0, 1)).  The product is
+// formed with an FMA error term and the lo part of n/(2 pi), so frac is
+// accurate to about 1e-7 cells even where x n / (2 pi) is ~1e3 (a plain
+// float product would lose ~3e-5 cells there, i.e. a phase error of
+// N_i * 2^-24 rad, the rounding law of Remark r:rounding).
+__device__ __forceinline__ void fold(float x, int n, float s_hi, float s_lo, double, int& cell,
+                                     float& frac) {
+  float p = x * s_hi;
+  float e = fmaf(x, s_hi, -p);
+  float corr = fmaf(x, s_lo, e);
+  float fl = floorf(p);
+  float fr = (p - fl) + corr;  // p - fl is exact
+  long long i = (long long)fl;
+  if (fr < 0.f) {
+    fr += 1.f;
+    --i;
+  }
+  if (fr >= 1.f) {
+    fr -= 1.f;
+    ++i;
+  }
+  cell = wrap_cell(i, n);
+  frac = fr;
+}
+__device__ __forceinline__ void fold(double x, int n, float, float, double s, int& cell,
+                                     double& frac) {
+  double p = x * s;
+  double fl = floor(p);
+  double fr = p - fl;
+  long long i = (long long)fl;
+  if (fr >= 1.0) {
+    fr -= 1.0;
+    ++i;
+  }
+  cell = wrap_cell(i, n);
+  frac = fr;
+}
+
+template <typename T>
+__device__ __forceinline__ T coord(int dim, int j, const T* x, const T* y, const T* z) {
+  return dim == 0 ? x[j] : (dim == 1 ? y[j] : z[j]);
+}
+
+template <typename T>
+__global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict__ y,
+                             const T* __restrict__ z, Geom g, FoldConst fc, int chk,
+                             int* __restrict__ bin_count, int* __restrict__ pt_rank,
+                             int* __restrict__ err) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    int bin = 0, stride = 1;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (i < g.d) {
+        T xv = coord<T>(i, j, x, y, z);
+        if (chk) bad |= !(fabs(xv) <= (T)kThreePi);
+        int cell;
+        T fr;
+        fold(xv, g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
+        bin += (cell / g.B[i]) * stride;
+        stride *= g.nb[i];
+      }
+    }
+    if (chk && bad) atomicCAS(err, 0, NUFFT_ERR_OUT_OF_RANGE);
+    pt_rank[j] = atomicAdd(&bin_count[bin], 1);
+  }
+}
+
+// Exclusive scans of the bin counts and of the per-bin subproblem counts, in
+// one block: each thread owns a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, const int* __restrict__ cnt,
+                                               int* __restrict__ start, int* __restrict__ sub_first,
+                                               int* __restrict__ nsub) {
+  __shared__ long long wsum_p[32], wsum_s[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int chunk = (nbins + nt - 1) / nt;
+  const int b0 = min(nbins, tid * chunk), b1 = min(nbins, b0 + chunk);
+  long long sp = 0, ss = 0;
+  for (int b = b0; b < b1; ++b) {
+    int c = cnt[b];
+    sp += c;
+    ss += (c + maxsub - 1) / maxsub;
+  }
+  // block exclusive scan of (sp, ss)
+  const int lane = tid & 31, wid = tid >> 5;
+  long long ip = sp, is = ss;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long tp = __shfl_up_sync(0xffffffffu, ip, o);
+    long long ts = __shfl_up_sync(0xffffffffu, is, o);
+    if (lane >= o) {
+      ip += tp;
+      is += ts;
+    }
+  }
+  if (lane == 31) {
+    wsum_p[wid] = ip;
+    wsum_s[wid] = is;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    long long vp = lane < (nt >> 5) ? wsum_p[lane] : 0, vs = lane < (nt >> 5) ? wsum_s[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long tp = __shfl_up_sync(0xffffffffu, vp, o);
+      long long ts = __shfl_up_sync(0xffffffffu, vs, o);
+      if (lane >= o) {
+        vp += tp;
+        vs += ts;
+      }
+    }
+    wsum_p[lane] = vp;  // inclusive over warps
+    wsum_s[lane] = vs;
+  }
+  __syncthreads();
+  long long basep = (ip - sp) + (wid > 0 ? wsum_p[wid - 1] : 0);
+  long long bases = (is - ss) + (wid > 0 ? wsum_s[wid - 1] : 0);
+  for (int b = b0; b < b1; ++b) {
+    int c = cnt[b];
+    start[b] = (int)basep;
+    sub_first[b] = (int)bases;
+    basep += c;
+    bases += (c + maxsub - 1) / maxsub;
+  }
+  if (tid == nt - 1) *nsub = (int)bases;  // total number of subproblems
+}
+
+__global__ void k_sublist(int nbins, int maxsub, const int* __restrict__ cnt,
+                          const int* __restrict__ start, const int* __restrict__ sub_first,
+                          int* __restrict__ sub_bin, int* __restrict__ sub_pt0,
+                          int* __restrict__ sub_cnt) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+    int c = cnt[b];
+    int s0 = sub_first[b], p0 = start[b];
+    for (int k = 0; k * maxsub < c; ++k) {
+      sub_bin[s0 + k] = b;
+      sub_pt0[s0 + k] = p0 + k * maxsub;
+      sub_cnt[s0 + k] = min(maxsub, c - k * maxsub);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ y,
+                          const T* __restrict__ z, Geom g, FoldConst fc,
+                          const int* __restrict__ pt_rank, const int* __restrict__ start,
+                          typename Traits<T>::Rec* __restrict__ rec) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    typename Traits<T>::Rec r;
+    int bin = 0, stride = 1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      r.v[i] = T(0);
+      if (i < g.d) {
+        int cell;
+        T fr;
+        fold(coord<T>(i, j, x, y, z), g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
+        int b = cell / g.B[i];
+        r.v[i] = T(cell - b * g.B[i]) + fr;
+        bin += b * stride;
+        stride *= g.nb[i];
+      }
+    }
+    r.idx = j;
+    rec[start[bin] + pt_rank[j]] = r;
+  }
+}
+
+int grid_for(int64_t work, int threads) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sms * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, const void* y,
+                     const void* z, int chk, int* bin_count, int* bin_start, int* sub_first,
+                     int* pt_rank, void* rec, int* sub_bin, int* sub_pt0, int* sub_cnt, int* nsub,
+                     int* err, cudaStream_t st, cudaEvent_t* ev) {
+  const T* xp = (const T*)x;
+  const T* yp = g.d > 1 ? (const T*)y : xp;
+  const T* zp = g.d > 2 ? (const T*)z : xp;
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], st);
+  if ((e = cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)g.nbins, st)) != cudaSuccess) return e;
+  if (M > 0) {
+    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, bin_count, pt_rank, err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[1], st);
+  k_scan<<<1, 1024, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start, sub_first, nsub);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_sublist<<<grid_for(g.nbins, 256), 256, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start,
+                                                     sub_first, sub_bin, sub_pt0, sub_cnt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[2], st);
+  if (M > 0) {
+    k_scatter<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, pt_rank, bin_start,
+                                                    (typename Traits<T>::Rec*)rec);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[3], st);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
+                          const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
+                          int* sub_first, int* /*pt_bin*/, int* pt_rank, void* rec, int* sub_bin,
+                          int* sub_pt0, int* sub_cnt, int* nsub, int* err, cudaStream_t st,
+                          cudaEvent_t* ev) {
+  if (dbl)
+    return setpts_t<double>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, pt_rank,
+                            rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev);
+  return setpts_t<float>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, pt_rank,
+                         rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev);
+}
+
+}  // namespace nufft

@@ -1,0 +1,121 @@
+// Diagonal correction between the fine grid and the mode array.
+//
+// Type 1, step 3 (Eq. (pb1), Eq. (pk)): f_k = p_{k_1} ... p_{k_d} b^_{k mod n}
+//   for k in I_N -- truncation to the central modes, correction and reordering
+//   in one pass (k_deconv, one thread per output mode).
+// Type 2, step 1 (Sec. 3.2): b^_{k mod n} = p_k f_k for k in I_N and 0 on the
+//   rest of the fine grid (k_precorrect, one thread per fine-grid cell, so the
+//   zero padding and the scatter are a single write of the grid).
+// p_{k_i} = 2 / (w phi^(alpha_i k_i)) come from the host (Eq. (pk1)) as one
+// array per dimension indexed by k_i + floor(N_i / 2).
+#include "nufft_internal.cuh"
+
+namespace nufft {
+namespace {
+
+// mode array position -> k (modeord 0: increasing k; 1: FFT order)
+__device__ __forceinline__ int pos_to_k(int m, int N, int modeord) {
+  if (modeord == 0) return m - N / 2;
+  return (m < N - N / 2) ? m : m - N;
+}
+// k -> mode array position
+__device__ __forceinline__ int k_to_pos(int k, int N, int modeord) {
+  if (modeord == 0) return k + N / 2;
+  return k >= 0 ? k : k + N;
+}
+
+template <typename T>
+__global__ void k_deconv(ModeGeom m, const typename Traits<T>::C* __restrict__ grid,
+                         typename Traits<T>::C* __restrict__ f, const T* __restrict__ p1,
+                         const T* __restrict__ p2, const T* __restrict__ p3) {
+  using C = typename Traits<T>::C;
+  for (int m3 = blockIdx.z; m3 < m.N[2]; m3 += gridDim.z)
+  for (int m2 = blockIdx.y; m2 < m.N[1]; m2 += gridDim.y) {
+  const int k2 = pos_to_k(m2, m.N[1], m.modeord), k3 = pos_to_k(m3, m.N[2], m.modeord);
+  const int l2 = k2 < 0 ? k2 + m.n[1] : k2, l3 = k3 < 0 ? k3 + m.n[2] : k3;
+  const T p23 = p2[k2 + m.N[1] / 2] * p3[k3 + m.N[2] / 2];
+  const C* grow = grid + ((long long)l3 * m.n[1] + l2) * (long long)m.n[0];
+  C* frow = f + ((long long)m3 * m.N[1] + m2) * (long long)m.N[0];
+  for (int m1 = blockIdx.x * blockDim.x + threadIdx.x; m1 < m.N[0]; m1 += gridDim.x * blockDim.x) {
+    const int k1 = pos_to_k(m1, m.N[0], m.modeord);
+    const int l1 = k1 < 0 ? k1 + m.n[0] : k1;
+    const T p = p23 * p1[k1 + m.N[0] / 2];
+    const C b = grow[l1];
+    C o;
+    o.x = b.x * p;
+    o.y = b.y * p;
+    frow[m1] = o;
+  }
+  }
+}
+
+template <typename T>
+__global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict__ f,
+                             typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
+                             const T* __restrict__ p2, const T* __restrict__ p3) {
+  using C = typename Traits<T>::C;
+  for (int l3 = blockIdx.z; l3 < m.n[2]; l3 += gridDim.z)
+  for (int l2 = blockIdx.y; l2 < m.n[1]; l2 += gridDim.y) {
+  // fine-grid index l <-> mode k = l (l < N - N/2) or l - n (l >= n - N/2)
+  const int k2 = l2 < m.N[1] - m.N[1] / 2 ? l2 : l2 - m.n[1];
+  const int k3 = l3 < m.N[2] - m.N[2] / 2 ? l3 : l3 - m.n[2];
+  const bool in23 = (k2 >= -(m.N[1] / 2)) && (k3 >= -(m.N[2] / 2));
+  C* grow = grid + ((long long)l3 * m.n[1] + l2) * (long long)m.n[0];
+  const C zero = {T(0), T(0)};
+  if (!in23) {
+    for (int l1 = blockIdx.x * blockDim.x + threadIdx.x; l1 < m.n[0]; l1 += gridDim.x * blockDim.x) grow[l1] = zero;
+    continue;
+  }
+  const T p23 = p2[k2 + m.N[1] / 2] * p3[k3 + m.N[2] / 2];
+  const C* frow = f + ((long long)k_to_pos(k3, m.N[2], m.modeord) * m.N[1] + k_to_pos(k2, m.N[1], m.modeord)) *
+                          (long long)m.N[0];
+  for (int l1 = blockIdx.x * blockDim.x + threadIdx.x; l1 < m.n[0]; l1 += gridDim.x * blockDim.x) {
+    const int k1 = l1 < m.N[0] - m.N[0] / 2 ? l1 : l1 - m.n[0];
+    C o = zero;
+    if (k1 >= -(m.N[0] / 2)) {
+      const T p = p23 * p1[k1 + m.N[0] / 2];
+      const C v = frow[k_to_pos(k1, m.N[0], m.modeord)];
+      o.x = v.x * p;
+      o.y = v.y * p;
+    }
+    grow[l1] = o;
+  }
+  }
+}
+
+dim3 row_grid(int len, int rows, int slabs, int threads) {
+  int bx = (len + threads - 1) / threads;
+  if (bx > 65535) bx = 65535;
+  return dim3(bx, rows < 65535 ? rows : 65535, slabs < 65535 ? slabs : 65535);
+}
+
+template <typename T>
+cudaError_t deconv_t(const ModeGeom& m, const void* grid, void* f, const void* p1, const void* p2,
+                     const void* p3, cudaStream_t st) {
+  k_deconv<T><<<row_grid(m.N[0], m.N[1], m.N[2], 256), 256, 0, st>>>(
+      m, (const typename Traits<T>::C*)grid, (typename Traits<T>::C*)f, (const T*)p1, (const T*)p2,
+      (const T*)p3);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t precorrect_t(const ModeGeom& m, const void* f, void* grid, const void* p1,
+                         const void* p2, const void* p3, cudaStream_t st) {
+  k_precorrect<T><<<row_grid(m.n[0], m.n[1], m.n[2], 256), 256, 0, st>>>(
+      m, (const typename Traits<T>::C*)f, (typename Traits<T>::C*)grid, (const T*)p1, (const T*)p2,
+      (const T*)p3);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_deconv(bool dbl, const ModeGeom& m, const void* grid, void* f, const void* p1,
+                          const void* p2, const void* p3, cudaStream_t st) {
+  return dbl ? deconv_t<double>(m, grid, f, p1, p2, p3, st) : deconv_t<float>(m, grid, f, p1, p2, p3, st);
+}
+cudaError_t launch_precorrect(bool dbl, const ModeGeom& m, const void* f, void* grid, const void* p1,
+                              const void* p2, const void* p3, cudaStream_t st) {
+  return dbl ? precorrect_t<double>(m, f, grid, p1, p2, p3, st)
+             : precorrect_t<float>(m, f, grid, p1, p2, p3, st);
+}
+
+}  // namespace nufft

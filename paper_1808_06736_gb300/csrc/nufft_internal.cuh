@@ -1,0 +1,122 @@
+// Internal declarations shared by the translation units of libnufft_gb300.
+// Nothing here is part of the C ABI (include/nufft_gb300.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+
+#include "../../include/nufft_gb300.h"
+
+namespace nufft {
+
+// Geometry of the fine grid, the bins and the shared-memory tiles; passed by
+// value to every kernel.  Dimensions above d have n = B = T = nb = 1.
+struct Geom {
+  int d;         // 1, 2 or 3
+  int w;         // kernel width in fine-grid cells
+  int half;      // floor(w / 2): tile origin = bin origin - half
+  int n[3];      // fine-grid size per dimension
+  int B[3];      // bin extent per dimension
+  int nb[3];     // bins per dimension = ceil(n / B)
+  int T[3];      // tile extent per dimension = B + w
+  int nbins;     // nb[0] nb[1] nb[2]
+  int ntile;     // T[0] T[1] T[2]
+  int maxsub;    // most points in one subproblem
+};
+
+// One binned point: coordinates relative to the origin of its bin, in units
+// of fine-grid cells (v in [0, B)), and its index in the caller's arrays.
+struct alignas(16) RecF {
+  float v[3];
+  int idx;
+};
+struct alignas(16) RecD {
+  double v[3];
+  int idx;
+  int pad;
+};
+
+template <typename T>
+struct Traits;
+template <>
+struct Traits<float> {
+  using C = float2;
+  using Rec = RecF;
+};
+template <>
+struct Traits<double> {
+  using C = double2;
+  using Rec = RecD;
+};
+
+// Device arrays produced by setpts and read by spread / interp.
+struct Sorted {
+  const void* rec;     // RecF / RecD [M], in bin order
+  const int* sub_bin;  // [nsub] bin of each subproblem
+  const int* sub_pt0;  // [nsub] first record of each subproblem
+  const int* sub_cnt;  // [nsub] number of records
+  const int* nsub;     // device scalar
+};
+
+// --- setpts (binsort.cu) ------------------------------------------------------
+struct FoldConst {  // n / (2 pi) per dimension split into a hi and lo part
+  double s[3];
+  float s_hi[3];
+  float s_lo[3];
+};
+FoldConst make_fold_const(const Geom& g);
+
+// Enqueue the whole setpts pipeline.  Work arrays are owned by the plan.
+cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
+                          const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
+                          int* sub_first, int* pt_bin, int* pt_rank, void* rec, int* sub_bin,
+                          int* sub_pt0, int* sub_cnt, int* nsub, int* err, cudaStream_t st,
+                          cudaEvent_t* ev /* 4 events or nullptr */);
+
+// --- spread / interp (spread_interp_*.cu) --------------------------------------
+struct LaunchCfg {
+  int threads;
+  int blocks;   // persistent grid
+  size_t smem;  // dynamic shared memory bytes
+};
+// smem bytes a spread / interp kernel needs for this geometry
+size_t spread_smem_bytes(bool dbl, const Geom& g, int threads);
+size_t interp_smem_bytes(bool dbl, const Geom& g, int threads);
+// configure (max dynamic smem attribute) and size the persistent grid
+cudaError_t spread_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg);
+cudaError_t interp_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg);
+
+cudaError_t launch_spread(bool dbl, const Geom& g, double beta, const Sorted& s, const void* c,
+                          void* grid, int* work, const LaunchCfg& cfg, cudaStream_t st);
+cudaError_t launch_interp(bool dbl, const Geom& g, double beta, const Sorted& s, const void* grid,
+                          void* c, int* work, const LaunchCfg& cfg, cudaStream_t st);
+
+// per-precision, per-dimension entry points (one translation unit each)
+#define NUFFT_DECL_SI(P, D)                                                                      \
+  cudaError_t spread_##P##_d##D(const Geom&, double, const Sorted&, const void*, void*, int*,   \
+                                const LaunchCfg&, cudaStream_t, bool configure_only);           \
+  cudaError_t interp_##P##_d##D(const Geom&, double, const Sorted&, const void*, void*, int*,   \
+                                const LaunchCfg&, cudaStream_t, bool configure_only);
+NUFFT_DECL_SI(f32, 1)
+NUFFT_DECL_SI(f32, 2)
+NUFFT_DECL_SI(f32, 3)
+NUFFT_DECL_SI(f64, 1)
+NUFFT_DECL_SI(f64, 2)
+NUFFT_DECL_SI(f64, 3)
+#undef NUFFT_DECL_SI
+
+// --- deconvolve / pre-correct (deconv.cu) -------------------------------------
+struct ModeGeom {
+  int d;
+  int N[3];   // modes per dimension (1 above d)
+  int n[3];   // fine grid per dimension
+  int modeord;
+};
+cudaError_t launch_deconv(bool dbl, const ModeGeom& m, const void* grid, void* f, const void* p1,
+                          const void* p2, const void* p3, cudaStream_t st);
+cudaError_t launch_precorrect(bool dbl, const ModeGeom& m, const void* f, void* grid, const void* p1,
+                              const void* p2, const void* p3, cudaStream_t st);
+
+}  // namespace nufft

@@ -1,0 +1,567 @@
+// Host side of libnufft_gb300: the C ABI of include/nufft_gb300.h.
+//
+// makeplan  parameters (Eq. (params), Sec. 3.1.1), correction factors
+//           (Eq. (pk1)/(pk) via the Gauss-Legendre rule of Eq. (quad) with
+//           phase winding), fine grid, cuFFT plan
+// setpts    binning pipeline (binsort.cu)
+// execute   type 1: zero grid, spread, FFT, deconvolve
+//           type 2: pre-correct/pad, FFT, interpolate
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nufft_internal.cuh"
+
+using namespace nufft;
+
+struct nufft_plan_s {
+  int type = 0, dim = 0, isign = 0, ntransf = 1, prec = 0;
+  nufft_opts opts;
+  int64_t N[3] = {1, 1, 1};
+  int64_t Ntot = 1;
+  int w = 0;
+  double beta = 0;
+  Geom g;
+  int64_t ngrid = 1;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool dbl = false;
+  size_t csize = 8;  // bytes per complex
+  void* grid = nullptr;
+  void* pk[3] = {nullptr, nullptr, nullptr};
+  int* bin_count = nullptr;
+  int* bin_start = nullptr;
+  int* sub_first = nullptr;
+  int* small = nullptr;  // [0] error word, [1] nsub, [2] work counter
+  int64_t M = -1;
+  int64_t Mcap = 0;
+  int* pt_rank = nullptr;
+  void* rec = nullptr;
+  int64_t subcap = 0;
+  int* sub_bin = nullptr;
+  int* sub_pt0 = nullptr;
+  int* sub_cnt = nullptr;
+  cufftHandle fft = 0;
+  bool fft_ok = false;
+  LaunchCfg spread_cfg{0, 0, 0}, interp_cfg{0, 0, 0};
+  cudaEvent_t ev[8];
+  bool ev_ok = false;
+  int last_steps = 0;  // which timing slots the last call filled: 1 setpts, 2 execute
+};
+
+namespace {
+
+const double kPi = 3.141592653589793238462643383279502884;
+
+#define CUDA_TRY(x)                          \
+  do {                                       \
+    if ((x) != cudaSuccess) return NUFFT_ERR_CUDA; \
+  } while (0)
+
+int64_t next235_impl(int64_t m) {
+  if (m < 1) return -1;
+  for (int64_t n = m; n < ((int64_t)1 << 62); ++n) {
+    int64_t r = n;
+    while (r % 2 == 0) r /= 2;
+    while (r % 3 == 0) r /= 3;
+    while (r % 5 == 0) r /= 5;
+    if (r == 1) return n;
+  }
+  return -1;
+}
+
+// Eq. (params): w = ceil(log10(1/eps)) + 1 (guarded against log10 rounding at
+// exact powers of ten), clamped to [2, 16]; beta = 2.30 w.
+int width_for(double eps) {
+  double lw = std::ceil(std::log10(1.0 / eps) - 1e-9) + 1.0;
+  if (!(lw >= 2.0)) lw = 2.0;
+  if (lw > 16.0) lw = 16.0;
+  return (int)lw;
+}
+
+int choose_params_impl(int dim, const int64_t* N, double eps, int prec, int* w, double* beta, int64_t* n) {
+  if (dim < 1 || dim > 3 || !N || !(eps > 0.0) || !std::isfinite(eps) ||
+      (prec != NUFFT_C64 && prec != NUFFT_C128))
+    return NUFFT_ERR_BAD_ARG;
+  for (int i = 0; i < dim; ++i)
+    if (N[i] < 1) return NUFFT_ERR_BAD_ARG;
+  int ww = width_for(eps);
+  if (w) *w = ww;
+  if (beta) *beta = 2.30 * ww;
+  for (int i = 0; i < dim; ++i) {
+    int64_t m = std::max<int64_t>(2 * N[i], 2 * (int64_t)ww);  // sigma = 2
+    int64_t v = next235_impl(m);
+    if (v < 0) return NUFFT_ERR_BAD_ARG;
+    if (n) n[i] = v;
+  }
+  double floor_eps = (prec == NUFFT_C64) ? 1e-6 : 1e-15;
+  return (eps < floor_eps) ? NUFFT_WARN_EPS_TOO_SMALL : NUFFT_OK;
+}
+
+// Positive nodes / weights of the 2p-point Gauss-Legendre rule by Newton's
+// method on the three-term Legendre recurrence.
+void gauss_legendre_positive(int p, std::vector<double>& q, std::vector<double>& wq) {
+  const int m = 2 * p;
+  q.assign(p, 0.0);
+  wq.assign(p, 0.0);
+  for (int i = 0; i < p; ++i) {
+    // i-th largest root; classical initial guess
+    double x = std::cos(kPi * (i + 0.75) / (m + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= m; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = m * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    // recompute the derivative at the converged node
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= m; ++k) {
+      double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = m * (x * p1 - p0) / (x * x - 1.0);
+    q[i] = x;
+    wq[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// Eq. (pk1) with Eq. (quad): p_k = 2 / (w phi^(alpha k)),
+// phi^(xi) = 2 sum_j w_j phi(q_j) cos(xi q_j) over the p positive nodes,
+// p = ceil(1.5 w + 2).  cos(alpha k q_j) by phase winding over k (a complex
+// multiply per step), re-anchored with a direct cos/sin every 256 steps.
+int correction_impl(int64_t N, int64_t n, int w, double beta, double* out) {
+  if (N < 1 || n < 1 || w < 2 || w > 16 || !out) return NUFFT_ERR_BAD_ARG;
+  const int p = (int)std::ceil(1.5 * w + 2.0);
+  std::vector<double> q, wq;
+  gauss_legendre_positive(p, q, wq);
+  std::vector<double> a(p);
+  for (int j = 0; j < p; ++j) a[j] = 2.0 * wq[j] * std::exp(beta * (std::sqrt(1.0 - q[j] * q[j]) - 1.0));
+  const double alpha = kPi * w / (double)n;
+  const int64_t kmax = N - 1 - N / 2;   // largest k; |k| <= N/2
+  const int64_t kabs = std::max<int64_t>(kmax, N / 2);
+  std::vector<double> ft(kabs + 1, 0.0);
+  std::vector<double> cr(p), ci(p), zr(p), zi(p);
+  for (int j = 0; j < p; ++j) {
+    cr[j] = 1.0;
+    ci[j] = 0.0;
+    zr[j] = std::cos(alpha * q[j]);
+    zi[j] = std::sin(alpha * q[j]);
+  }
+  for (int64_t k = 0; k <= kabs; ++k) {
+    if (k % 256 == 0 && k > 0)
+      for (int j = 0; j < p; ++j) {
+        cr[j] = std::cos(alpha * (double)k * q[j]);
+        ci[j] = std::sin(alpha * (double)k * q[j]);
+      }
+    double s = 0.0;
+    for (int j = 0; j < p; ++j) s += a[j] * cr[j];
+    ft[k] = s;
+    for (int j = 0; j < p; ++j) {
+      double r = cr[j] * zr[j] - ci[j] * zi[j];
+      double i = cr[j] * zi[j] + ci[j] * zr[j];
+      cr[j] = r;
+      ci[j] = i;
+    }
+  }
+  for (int64_t m = 0; m < N; ++m) {
+    int64_t k = m - N / 2;
+    out[m] = 2.0 / (w * ft[k < 0 ? -k : k]);
+  }
+  return NUFFT_OK;
+}
+
+// Bin shapes in order of preference; the first whose spread kernel fits the
+// shared-memory budget wins.
+void choose_bins(Geom& g, bool dbl, const nufft_opts& o) {
+  static const int c3[][3] = {{16, 8, 8}, {8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {4, 4, 4}};
+  static const int c2[][3] = {{32, 32, 1}, {32, 16, 1}, {16, 16, 1}, {16, 8, 1}, {8, 8, 1}};
+  static const int c1[][3] = {{1024, 1, 1}, {512, 1, 1}, {256, 1, 1}, {128, 1, 1}, {64, 1, 1}};
+  const int(*c)[3] = g.d == 3 ? c3 : (g.d == 2 ? c2 : c1);
+  const size_t budget = 110 * 1024;
+  for (int k = 0; k < 5; ++k) {
+    for (int i = 0; i < 3; ++i) {
+      int b = (o.bin_size[i] > 0 && i < g.d) ? o.bin_size[i] : c[k][i];
+      if (i >= g.d) b = 1;
+      g.B[i] = std::max(1, std::min(b, g.n[i]));
+    }
+    for (int i = 0; i < 3; ++i) {
+      g.T[i] = (i < g.d) ? g.B[i] + g.w : 1;
+      g.nb[i] = (g.n[i] + g.B[i] - 1) / g.B[i];
+    }
+    g.ntile = g.T[0] * g.T[1] * g.T[2];
+    g.nbins = g.nb[0] * g.nb[1] * g.nb[2];
+    size_t need = spread_smem_bytes(dbl, g, 256);
+    if (need <= budget || (o.bin_size[0] > 0)) break;
+  }
+}
+
+int fail(nufft_plan p, int code) {
+  nufft_destroy(p);
+  return code;
+}
+
+template <typename P>
+cudaError_t dev_alloc(P** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc((void**)ptr, bytes);
+}
+
+}  // namespace
+
+namespace nufft {
+
+size_t spread_smem_bytes(bool dbl, const Geom& g, int) {
+  size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8, ct = dbl ? 8 : 4;
+  return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc +
+         (size_t)g.maxsub * (g.d * ct + 4 + 3 * 2);
+}
+size_t interp_smem_bytes(bool dbl, const Geom& g, int) {
+  size_t cc = dbl ? 16 : 8, ct = dbl ? 8 : 4;
+  return (size_t)g.ntile * cc + (size_t)g.maxsub * (g.d * ct + 4 + 3 * 2);
+}
+
+static cudaError_t si_dispatch(bool spread, bool dbl, const Geom& g, double beta, const Sorted& s,
+                               const void* a, void* b, int* work, const LaunchCfg& cfg,
+                               cudaStream_t st, bool conf) {
+  if (spread) {
+    if (!dbl) {
+      if (g.d == 1) return spread_f32_d1(g, beta, s, a, b, work, cfg, st, conf);
+      if (g.d == 2) return spread_f32_d2(g, beta, s, a, b, work, cfg, st, conf);
+      return spread_f32_d3(g, beta, s, a, b, work, cfg, st, conf);
+    }
+    if (g.d == 1) return spread_f64_d1(g, beta, s, a, b, work, cfg, st, conf);
+    if (g.d == 2) return spread_f64_d2(g, beta, s, a, b, work, cfg, st, conf);
+    return spread_f64_d3(g, beta, s, a, b, work, cfg, st, conf);
+  }
+  if (!dbl) {
+    if (g.d == 1) return interp_f32_d1(g, beta, s, a, b, work, cfg, st, conf);
+    if (g.d == 2) return interp_f32_d2(g, beta, s, a, b, work, cfg, st, conf);
+    return interp_f32_d3(g, beta, s, a, b, work, cfg, st, conf);
+  }
+  if (g.d == 1) return interp_f64_d1(g, beta, s, a, b, work, cfg, st, conf);
+  if (g.d == 2) return interp_f64_d2(g, beta, s, a, b, work, cfg, st, conf);
+  return interp_f64_d3(g, beta, s, a, b, work, cfg, st, conf);
+}
+
+static cudaError_t configure(bool spread, bool dbl, const Geom& g, int threads, LaunchCfg* cfg) {
+  cfg->threads = threads;
+  cfg->smem = spread ? spread_smem_bytes(dbl, g, threads) : interp_smem_bytes(dbl, g, threads);
+  cfg->blocks = 0;
+  Sorted s{};
+  cudaError_t e = si_dispatch(spread, dbl, g, 0.0, s, nullptr, nullptr, nullptr, *cfg, nullptr, true);
+  if (e != cudaSuccess) return e;
+  int per_sm = cfg->blocks, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cfg->blocks = per_sm * sms;
+  return cudaSuccess;
+}
+
+cudaError_t spread_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg) {
+  return configure(true, dbl, g, threads, cfg);
+}
+cudaError_t interp_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg) {
+  return configure(false, dbl, g, threads, cfg);
+}
+cudaError_t launch_spread(bool dbl, const Geom& g, double beta, const Sorted& s, const void* c,
+                          void* grid, int* work, const LaunchCfg& cfg, cudaStream_t st) {
+  return si_dispatch(true, dbl, g, beta, s, c, grid, work, cfg, st, false);
+}
+cudaError_t launch_interp(bool dbl, const Geom& g, double beta, const Sorted& s, const void* grid,
+                          void* c, int* work, const LaunchCfg& cfg, cudaStream_t st) {
+  return si_dispatch(false, dbl, g, beta, s, grid, c, work, cfg, st, false);
+}
+
+}  // namespace nufft
+
+extern "C" {
+
+int nufft_default_opts(nufft_opts* o) {
+  if (!o) return NUFFT_ERR_BAD_ARG;
+  std::memset(o, 0, sizeof(*o));
+  return NUFFT_OK;
+}
+
+int64_t nufft_next235(int64_t m) { return next235_impl(m); }
+
+int nufft_choose_params(int dim, const int64_t* nmodes, double eps, int prec, int* w, double* beta,
+                        int64_t* n) {
+  return choose_params_impl(dim, nmodes, eps, prec, w, beta, n);
+}
+
+int nufft_correction_factors(int64_t N, int64_t n, int w, double beta, double* out) {
+  return correction_impl(N, n, w, beta, out);
+}
+
+const char* nufft_strerror(int code) {
+  switch (code) {
+    case NUFFT_OK: return "success";
+    case NUFFT_WARN_EPS_TOO_SMALL: return "warning: eps below what this precision can deliver";
+    case NUFFT_ERR_BAD_ARG: return "invalid argument";
+    case NUFFT_ERR_OUT_OF_RANGE: return "a point lies outside [-3 pi, 3 pi] or is not finite";
+    case NUFFT_ERR_ALLOC: return "device allocation failed";
+    case NUFFT_ERR_CUDA: return "CUDA runtime error";
+    case NUFFT_ERR_CUFFT: return "cuFFT error";
+    case NUFFT_ERR_NOT_SET: return "execute called before setpts";
+    case NUFFT_ERR_TOO_BIG: return "problem too large for the index types";
+    default: return "unknown status";
+  }
+}
+
+int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntransf, double eps,
+                   int prec, void* stream, const nufft_opts* opts, nufft_plan* out) {
+  if (!out) return NUFFT_ERR_BAD_ARG;
+  *out = nullptr;
+  if ((type != 1 && type != 2) || (isign != 1 && isign != -1) || ntransf < 1) return NUFFT_ERR_BAD_ARG;
+  int w;
+  double beta;
+  int64_t n[3] = {1, 1, 1};
+  int warn = choose_params_impl(dim, nmodes, eps, prec, &w, &beta, n);
+  if (warn < 0) return warn;
+  for (int i = 0; i < dim; ++i)
+    if (nmodes[i] > (1 << 29) || n[i] > (1 << 30)) return NUFFT_ERR_TOO_BIG;
+
+  nufft_plan p = new (std::nothrow) nufft_plan_s();
+  if (!p) return NUFFT_ERR_ALLOC;
+  p->type = type;
+  p->dim = dim;
+  p->isign = isign;
+  p->ntransf = ntransf;
+  p->prec = prec;
+  p->dbl = (prec == NUFFT_C128);
+  p->csize = p->dbl ? 16 : 8;
+  if (opts) p->opts = *opts;
+  else nufft_default_opts(&p->opts);
+  p->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
+  p->w = w;
+  p->beta = beta;
+  p->Ntot = 1;
+  p->ngrid = 1;
+  for (int i = 0; i < 3; ++i) {
+    p->N[i] = i < dim ? nmodes[i] : 1;
+    p->Ntot *= p->N[i];
+    p->ngrid *= n[i];
+  }
+  Geom& g = p->g;
+  g.d = dim;
+  g.w = w;
+  g.half = w / 2;
+  for (int i = 0; i < 3; ++i) g.n[i] = (int)n[i];
+  g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
+  choose_bins(g, p->dbl, p->opts);
+  int threads = p->opts.threads > 0 ? p->opts.threads : 256;
+  if (threads % 32 != 0 || threads > 256) return fail(p, NUFFT_ERR_BAD_ARG);
+
+  // device buffers owned by the plan
+  if (dev_alloc(&p->grid, p->ngrid * p->csize) != cudaSuccess) return fail(p, NUFFT_ERR_ALLOC);
+  size_t rs = p->dbl ? 8 : 4;
+  for (int i = 0; i < 3; ++i) {
+    std::vector<double> pk((size_t)p->N[i], 1.0);
+    if (i < dim && correction_impl(p->N[i], n[i], w, beta, pk.data()) != NUFFT_OK) return fail(p, NUFFT_ERR_BAD_ARG);
+    if (dev_alloc(&p->pk[i], (size_t)p->N[i] * rs) != cudaSuccess) return fail(p, NUFFT_ERR_ALLOC);
+    if (p->dbl) {
+      if (cudaMemcpy(p->pk[i], pk.data(), pk.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(p, NUFFT_ERR_CUDA);
+    } else {
+      std::vector<float> pf(pk.begin(), pk.end());
+      if (cudaMemcpy(p->pk[i], pf.data(), pf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(p, NUFFT_ERR_CUDA);
+    }
+  }
+  if (dev_alloc(&p->bin_count, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
+      dev_alloc(&p->bin_start, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
+      dev_alloc(&p->sub_first, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
+      dev_alloc(&p->small, sizeof(int) * 4) != cudaSuccess)
+    return fail(p, NUFFT_ERR_ALLOC);
+  if (cudaMemset(p->small, 0, sizeof(int) * 4) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
+
+  cudaError_t e = (type == 1) ? spread_config(p->dbl, g, threads, &p->spread_cfg)
+                              : interp_config(p->dbl, g, threads, &p->interp_cfg);
+  if (e != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
+
+  // cuFFT: dimensions slowest first
+  int nn[3];
+  for (int i = 0; i < dim; ++i) nn[i] = (int)n[dim - 1 - i];
+  if (cufftPlanMany(&p->fft, dim, nn, nullptr, 1, 0, nullptr, 1, 0, p->dbl ? CUFFT_Z2Z : CUFFT_C2C, 1) !=
+      CUFFT_SUCCESS)
+    return fail(p, NUFFT_ERR_CUFFT);
+  p->fft_ok = true;
+  if (cufftSetStream(p->fft, p->stream) != CUFFT_SUCCESS) return fail(p, NUFFT_ERR_CUFFT);
+  if (p->opts.debug) {
+    for (int i = 0; i < 8; ++i)
+      if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
+    p->ev_ok = true;
+  }
+  *out = p;
+  return warn;
+}
+
+int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const void* z) {
+  if (!p || M < 0) return NUFFT_ERR_BAD_ARG;
+  if (M > 0 && (!x || (p->dim > 1 && !y) || (p->dim > 2 && !z))) return NUFFT_ERR_BAD_ARG;
+  if (M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_TOO_BIG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  const Geom& g = p->g;
+  if (M > p->Mcap) {
+    cudaFree(p->pt_rank);
+    cudaFree(p->rec);
+    p->pt_rank = nullptr;
+    p->rec = nullptr;
+    p->Mcap = 0;
+    size_t rsz = p->dbl ? sizeof(RecD) : sizeof(RecF);
+    if (dev_alloc(&p->pt_rank, sizeof(int) * (size_t)M) != cudaSuccess ||
+        dev_alloc(&p->rec, rsz * (size_t)M) != cudaSuccess)
+      return NUFFT_ERR_ALLOC;
+    p->Mcap = M;
+  }
+  int64_t need = std::min<int64_t>(g.nbins, M) + M / g.maxsub + 1;
+  if (need > p->subcap) {
+    cudaFree(p->sub_bin);
+    cudaFree(p->sub_pt0);
+    cudaFree(p->sub_cnt);
+    p->sub_bin = p->sub_pt0 = p->sub_cnt = nullptr;
+    p->subcap = 0;
+    if (dev_alloc(&p->sub_bin, sizeof(int) * (size_t)need) != cudaSuccess ||
+        dev_alloc(&p->sub_pt0, sizeof(int) * (size_t)need) != cudaSuccess ||
+        dev_alloc(&p->sub_cnt, sizeof(int) * (size_t)need) != cudaSuccess)
+      return NUFFT_ERR_ALLOC;
+    p->subcap = need;
+  }
+  FoldConst fc = make_fold_const(g);
+  cudaError_t e = launch_setpts(p->dbl, g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
+                                p->sub_first, nullptr, p->pt_rank, p->rec, p->sub_bin, p->sub_pt0,
+                                p->sub_cnt, p->small + 1, p->small + 0, p->stream,
+                                p->ev_ok ? p->ev : nullptr);
+  if (e != cudaSuccess) return NUFFT_ERR_CUDA;
+  p->M = M;
+  p->last_steps = 1;
+  return NUFFT_OK;
+}
+
+int nufft_execute(nufft_plan p, void* c, void* f) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  if (p->M < 0) return NUFFT_ERR_NOT_SET;
+  if (!f || (p->M > 0 && !c)) return NUFFT_ERR_BAD_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  const Geom& g = p->g;
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1};
+  ModeGeom mg;
+  mg.d = p->dim;
+  mg.modeord = p->opts.modeord ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    mg.N[i] = (int)p->N[i];
+    mg.n[i] = g.n[i];
+  }
+  const int dir = p->isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
+  cudaEvent_t* ev = p->ev_ok ? p->ev + 4 : nullptr;
+  for (int t = 0; t < p->ntransf; ++t) {
+    char* ct = (char*)c + (size_t)t * (size_t)p->M * p->csize;
+    char* ft = (char*)f + (size_t)t * (size_t)p->Ntot * p->csize;
+    if (ev && t == 0) cudaEventRecord(ev[0], p->stream);
+    if (p->type == 1) {
+      CUDA_TRY(cudaMemsetAsync(p->grid, 0, (size_t)p->ngrid * p->csize, p->stream));
+      if (p->M > 0) {
+        CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
+        CUDA_TRY(launch_spread(p->dbl, g, p->beta, s, ct, p->grid, p->small + 2, p->spread_cfg, p->stream));
+      }
+    } else {
+      CUDA_TRY(launch_precorrect(p->dbl, mg, ft, p->grid, p->pk[0], p->pk[1], p->pk[2], p->stream));
+    }
+    if (ev && t == 0) cudaEventRecord(ev[1], p->stream);
+    cufftResult r = p->dbl ? cufftExecZ2Z(p->fft, (cufftDoubleComplex*)p->grid, (cufftDoubleComplex*)p->grid, dir)
+                           : cufftExecC2C(p->fft, (cufftComplex*)p->grid, (cufftComplex*)p->grid, dir);
+    if (r != CUFFT_SUCCESS) return NUFFT_ERR_CUFFT;
+    if (ev && t == 0) cudaEventRecord(ev[2], p->stream);
+    if (p->type == 1) {
+      CUDA_TRY(launch_deconv(p->dbl, mg, p->grid, ft, p->pk[0], p->pk[1], p->pk[2], p->stream));
+    } else if (p->M > 0) {
+      CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
+      CUDA_TRY(launch_interp(p->dbl, g, p->beta, s, p->grid, ct, p->small + 2, p->interp_cfg, p->stream));
+    }
+    if (ev && t == 0) cudaEventRecord(ev[3], p->stream);
+  }
+  p->last_steps = 2;
+  return NUFFT_OK;
+}
+
+int nufft_destroy(nufft_plan p) {
+  if (!p) return NUFFT_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(p->device);
+  cudaStreamSynchronize(p->stream);
+  if (p->fft_ok) cufftDestroy(p->fft);
+  if (p->ev_ok)
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(p->ev[i]);
+  void* bufs[] = {p->grid, p->pk[0], p->pk[1], p->pk[2], p->bin_count, p->bin_start, p->sub_first,
+                  p->small, p->pt_rank, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  cudaSetDevice(dev);
+  delete p;
+  return NUFFT_OK;
+}
+
+int nufft_get_status(nufft_plan p) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, p->small, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NUFFT_ERR_CUDA;
+  if (err != 0 && cudaMemset(p->small, 0, sizeof(int)) != cudaSuccess) return NUFFT_ERR_CUDA;
+  return err;
+}
+
+int nufft_get_timings(nufft_plan p, double* ms, int n) {
+  if (!p || !ms || n < 0) return NUFFT_ERR_BAD_ARG;
+  if (!p->ev_ok) return 0;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
+  int k = 0;
+  for (int i = 0; i < 6 && k < n; ++i, ++k) {
+    float v = 0.f;
+    int a = i < 3 ? i : i + 1;  // slots 0-3 setpts, 4-7 execute
+    if (cudaEventElapsedTime(&v, p->ev[a], p->ev[a + 1]) != cudaSuccess) v = -1.f;
+    ms[k] = v;
+  }
+  return k;
+}
+
+int nufft_plan_info(nufft_plan p, int* w, double* beta, int64_t* n, int* bins, int64_t* nsub) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  if (w) *w = p->w;
+  if (beta) *beta = p->beta;
+  for (int i = 0; i < p->dim; ++i) {
+    if (n) n[i] = p->g.n[i];
+    if (bins) bins[i] = p->g.B[i];
+  }
+  if (nsub) {
+    *nsub = 0;
+    if (p->M >= 0) {
+      if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
+      int v = 0;
+      if (cudaMemcpy(&v, p->small + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NUFFT_ERR_CUDA;
+      *nsub = v;
+    }
+  }
+  return NUFFT_OK;
+}
+
+}  // extern "C"

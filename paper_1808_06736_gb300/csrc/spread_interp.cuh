@@ -1,0 +1,514 @@
+// Spreading (type 1, Eq. (bl)) and interpolation (type 2, Eq. (interp)) with
+// the ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) (Eq. (ES)), one thread
+// block per subproblem (a bin, or a chunk of a crowded bin; cf. Sec. 5.2).
+//
+// Per subproblem a block
+//   1. stages the subproblem's point records in shared memory,
+//   2. counting-sorts them by the shared-memory bank of their stencil corner
+//      ("residue" = tile index mod 32) so that the 32 lanes of a warp, which
+//      take points a fixed stride apart in that order, touch 32 different
+//      banks on every access of the w^d loop,
+//   3. spreads into / gathers from a shared-memory tile that covers the bin
+//      plus a halo of floor(w/2) cells below and ceil(w/2) above, so the hot
+//      loop never wraps indices (the paper pads its cuboids by w/2 for the
+//      same reason, Sec. 5.2),
+//   4. (spread) adds the tile into the fine grid with periodic wrapping,
+//      (interp) writes each result to the caller's array.
+//
+// Spreading accumulates in shared memory in fixed point: every contribution
+// c_j psi is scaled by K / max_j |c_j| (K <= 2^22 for float, 2^51 for double,
+// and K * cnt < 2^31 resp. 2^63 so no cell can overflow), rounded to an
+// integer with one FMA against 1.5 * 2^23 (resp. 2^52) and added with an
+// integer atomic.  Integer shared-memory atomics are several times faster
+// than float ones on this GPU, the rounding error (<= max|c| 2^-23 per
+// contribution) is below that of float accumulation of the same sums, and
+// the tile result does not depend on the order of the atomics.
+#pragma once
+
+#include "nufft_internal.cuh"
+
+namespace nufft {
+
+template <typename T>
+struct Fixed;
+template <>
+struct Fixed<float> {
+  using I = int;
+  static constexpr double KMAX = 4194304.0;         // 2^22
+  static constexpr double IMAX = 2147483647.0;      // 2^31 - 1
+  __device__ static __forceinline__ int quant(float v) {  // v in [-2^22, 2^22]
+    return __float_as_int(fmaf(v, 1.0f, 12582912.0f)) - 0x4B400000;
+  }
+  __device__ static __forceinline__ float quant_fma(float a, float b) {
+    return fmaf(a, b, 12582912.0f);
+  }
+  __device__ static __forceinline__ int bits(float r) { return __float_as_int(r) - 0x4B400000; }
+  __device__ static __forceinline__ void add(int* p, int v) { atomicAdd(p, v); }
+};
+template <>
+struct Fixed<double> {
+  using I = long long;
+  static constexpr double KMAX = 2251799813685248.0;  // 2^51
+  static constexpr double IMAX = 9.2233720368547e18;  // just below 2^63
+  __device__ static __forceinline__ double quant_fma(double a, double b) {
+    return fma(a, b, 6755399441055744.0);  // 1.5 * 2^52
+  }
+  __device__ static __forceinline__ long long bits(double r) {
+    return __double_as_longlong(r) - 0x4338000000000000LL;
+  }
+  __device__ static __forceinline__ void add(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+  }
+};
+
+// ES kernel value.  Float: kpar = beta log2(e), one exp2.  Double: kpar = beta.
+__device__ __forceinline__ float es_eval(float z, float kpar) {
+  return exp2f(kpar * (sqrtf(fmaxf(1.0f - z * z, 0.0f)) - 1.0f));
+}
+__device__ __forceinline__ double es_eval(double z, double kpar) {
+  return exp(kpar * (sqrt(fmax(1.0 - z * z, 0.0)) - 1.0));
+}
+
+// The stencil of a coordinate u = cell + f starts at ceil(u - w/2), i.e. at
+// cell - floor(w/2) + step with step = [f > 0] (w even) or [f > 1/2] (w odd);
+// in the tile (origin = bin origin - floor(w/2)) that is local cell + step.
+template <int W, typename T>
+__device__ __forceinline__ int stencil_step(T f) {
+  return (W & 1) ? (f > T(0.5) ? 1 : 0) : (f > T(0) ? 1 : 0);
+}
+// kernel argument of node t: z = (t - floor(w/2) + step - f) * 2 / w
+template <int W, typename T>
+__device__ __forceinline__ T node_z(int t, int step, T f) {
+  return (T(t - W / 2 + step) - f) * (T(2) / T(W));
+}
+
+__device__ __forceinline__ void red_add(float2* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_add(double2* p, double a, double b) {
+  atomicAdd(&p->x, a);
+  atomicAdd(&p->y, b);
+}
+
+__device__ __forceinline__ int wrap_idx(int x, int n) {
+  if ((unsigned)x >= (unsigned)n) {
+    x %= n;
+    if (x < 0) x += n;
+  }
+  return x;
+}
+
+// Shared-memory layout common to both kernels (after the tile).
+template <typename T, int D>
+struct Stage {
+  T* v;                 // [maxsub * D] coordinates relative to the bin origin
+  int* idx;             // [maxsub] caller index
+  unsigned short* res;  // [maxsub] bank residue of the stencil corner
+  unsigned short* rank; // [maxsub] rank within its residue bucket
+  unsigned short* order;// [maxsub] records in residue order
+};
+
+template <typename T, int D>
+__host__ __device__ inline size_t stage_bytes(int maxsub) {
+  return (size_t)maxsub * (D * sizeof(T) + sizeof(int) + 3 * sizeof(unsigned short));
+}
+
+template <typename T, int D>
+__device__ __forceinline__ Stage<T, D> carve_stage(unsigned char* p, int maxsub) {
+  Stage<T, D> s;
+  s.v = reinterpret_cast<T*>(p);
+  p += (size_t)maxsub * D * sizeof(T);
+  s.idx = reinterpret_cast<int*>(p);
+  p += (size_t)maxsub * sizeof(int);
+  s.res = reinterpret_cast<unsigned short*>(p);
+  s.rank = s.res + maxsub;
+  s.order = s.rank + maxsub;
+  return s;
+}
+
+// Decode a bin index into its per-dimension tile origin (bin origin - floor(w/2)).
+__device__ __forceinline__ void tile_origin(const Geom& g, int bin, int* org) {
+  int b0 = bin % g.nb[0];
+  int r = bin / g.nb[0];
+  int b1 = r % g.nb[1];
+  int b2 = r / g.nb[1];
+  org[0] = b0 * g.B[0] - g.half;
+  org[1] = b1 * g.B[1] - g.half;
+  org[2] = b2 * g.B[2] - g.half;
+}
+
+// Load a record into the stage and bucket it by residue.  Returns nothing;
+// hist[] must be zero on entry.
+template <typename T, int D, int W>
+__device__ __forceinline__ void stage_point(const Geom& g, const typename Traits<T>::Rec& r, int q,
+                                            Stage<T, D>& st, int* hist) {
+  int base = 0, stride = 1;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    T v = r.v[d];
+    st.v[q * D + d] = v;
+    int il = min((int)v, g.B[d] - 1);
+    base += (il + stencil_step<W>(v - T(il))) * stride;
+    stride *= g.T[d];
+  }
+  st.idx[q] = r.idx;
+  int rr = base & 31;
+  st.res[q] = (unsigned short)rr;
+  st.rank[q] = (unsigned short)atomicAdd(&hist[rr], 1);
+}
+
+// hist -> exclusive bucket starts (warp 0), then order[] (all threads).
+template <typename T, int D>
+__device__ __forceinline__ void bucket_order(int cnt, Stage<T, D>& st, int* hist) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = hist[threadIdx.x], inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (threadIdx.x >= o) inc += t;
+    }
+    hist[threadIdx.x] = inc - v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) st.order[hist[st.res[q]] + st.rank[q]] = (unsigned short)q;
+  __syncthreads();
+}
+
+// Per-point kernel values along one dimension.
+template <typename T, int W>
+__device__ __forceinline__ void point_weights(T v, int B, T kpar, int& ts, T* k) {
+  int il = min((int)v, B - 1);
+  T f = v - T(il);
+  int s = stencil_step<W>(f);
+  ts = il + s;
+#pragma unroll
+  for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, s, f), kpar);
+}
+
+// ----------------------------------------------------------------- spread
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
+                                                const typename Traits<T>::C* __restrict__ c,
+                                                typename Traits<T>::C* __restrict__ grid,
+                                                int* __restrict__ work) {
+  using C = typename Traits<T>::C;
+  using Rec = typename Traits<T>::Rec;
+  using F = Fixed<T>;
+  using I = typename F::I;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int hist[32];
+  __shared__ int s_sub;
+  __shared__ I s_maxbits;
+
+  const int ntile = g.ntile, maxsub = g.maxsub;
+  I* tre = reinterpret_cast<I*>(smem);
+  I* tim = tre + ntile;
+  C* sc = reinterpret_cast<C*>(tim + ntile);  // staged strengths
+  Stage<T, D> st = carve_stage<T, D>(reinterpret_cast<unsigned char*>(sc + maxsub), maxsub);
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(s.rec);
+  const int T0 = g.T[0], T01 = g.T[0] * g.T[1];
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_sub = atomicAdd(work, 1);
+      s_maxbits = 0;
+    }
+    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int sub = s_sub;
+    if (sub >= *s.nsub) break;
+    const int bin = s.sub_bin[sub], p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      tre[t] = 0;
+      tim[t] = 0;
+    }
+    T mloc = T(0);
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      Rec r = rec[p0 + q];
+      stage_point<T, D, W>(g, r, q, st, hist);
+      C cv = c[r.idx];
+      sc[q] = cv;
+      mloc = fmax(mloc, fmax(fabs(cv.x), fabs(cv.y)));
+    }
+    // non-negative floats order like their bit patterns; NaN (all bits high) wins
+    if (!(mloc == mloc)) mloc = T(INFINITY);
+    if (sizeof(T) == 4)
+      atomicMax(reinterpret_cast<int*>(&s_maxbits), __float_as_int((float)mloc));
+    else
+      atomicMax(reinterpret_cast<unsigned long long*>(&s_maxbits),
+                (unsigned long long)__double_as_longlong((double)mloc));
+    bucket_order<T, D>(cnt, st, hist);
+
+    T maxabs;
+    if (sizeof(T) == 4)
+      maxabs = (T)__int_as_float((int)s_maxbits);
+    else
+      maxabs = (T)__longlong_as_double((long long)s_maxbits);
+    const double K = fmin(F::KMAX, floor(F::IMAX / (double)cnt) - 1.0);
+    T scale = T(0), inv = T(0);
+    if (maxabs > T(0) && maxabs < T(INFINITY)) {
+      scale = T(K / (double)maxabs);
+      inv = T((double)maxabs / K);
+    } else if (!(maxabs == T(0))) {
+      inv = T(NAN);  // non-finite strengths: make the whole tile NaN
+    }
+
+    const int Q = (cnt + 31) >> 5;
+    for (int sl = threadIdx.x; sl < (Q << 5); sl += blockDim.x) {
+      const int pos = (sl & 31) * Q + (sl >> 5);
+      if (pos >= cnt) continue;
+      const int q = st.order[pos];
+      T k0[W];
+      int ts0, ts1 = 0, ts2 = 0;
+      point_weights<T, W>(st.v[q * D], g.B[0], kpar, ts0, k0);
+      T k1[(D > 1) ? W : 1];
+      T f2 = T(0);
+      int st2 = 0;
+      if constexpr (D > 1) point_weights<T, W>(st.v[q * D + 1], g.B[1], kpar, ts1, k1);
+      else k1[0] = T(1);
+      if constexpr (D > 2) {
+        T v2 = st.v[q * D + 2];
+        int il2 = min((int)v2, g.B[2] - 1);
+        f2 = v2 - T(il2);
+        st2 = stencil_step<W>(f2);
+        ts2 = il2 + st2;
+      }
+      const C cv = sc[q];
+      const T cr = cv.x * scale, ci = cv.y * scale;
+      const int base = ts0 + T0 * ts1 + T01 * ts2;
+      constexpr int W1 = (D > 1) ? W : 1;
+      constexpr int W2 = (D > 2) ? W : 1;
+#pragma unroll 1
+      for (int l2 = 0; l2 < W2; ++l2) {
+        T k2 = T(1);
+        if constexpr (D > 2) k2 = es_eval(node_z<W>(l2, st2, f2), kpar);
+        const T cr2 = cr * k2, ci2 = ci * k2;
+#pragma unroll
+        for (int l1 = 0; l1 < W1; ++l1) {
+          const T cr1 = cr2 * k1[l1], ci1 = ci2 * k1[l1];
+          I* pr = tre + base + l1 * T0 + l2 * T01;
+          I* pi = tim + base + l1 * T0 + l2 * T01;
+#pragma unroll
+          for (int l0 = 0; l0 < W; ++l0) {
+            F::add(pr + l0, F::bits(F::quant_fma(cr1, k0[l0])));
+            F::add(pi + l0, F::bits(F::quant_fma(ci1, k0[l0])));
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // add the tile into the fine grid, wrapping periodically; rows of the
+    // tile are spread over the warps, a warp's lanes walk along x
+    int org[3];
+    tile_origin(g, bin, org);
+    const int nrows = ntile / T0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
+      const int t1 = row % g.T[1], t2 = row / g.T[1];
+      const long long gy = wrap_idx(org[1] + t1, g.n[1]);
+      const long long gz = wrap_idx(org[2] + t2, g.n[2]);
+      C* grow = grid + (gz * g.n[1] + gy) * (long long)g.n[0];
+      for (int t0 = lane; t0 < T0; t0 += 32) {
+        const int t = row * T0 + t0;
+        const I a = tre[t], b = tim[t];
+        if (a == 0 && b == 0) continue;
+        red_add(grow + wrap_idx(org[0] + t0, g.n[0]), T(a) * inv, T(b) * inv);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------- interp
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
+                                                const typename Traits<T>::C* __restrict__ grid,
+                                                typename Traits<T>::C* __restrict__ c,
+                                                int* __restrict__ work) {
+  using C = typename Traits<T>::C;
+  using Rec = typename Traits<T>::Rec;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int hist[32];
+  __shared__ int s_sub;
+
+  const int ntile = g.ntile, maxsub = g.maxsub;
+  C* tile = reinterpret_cast<C*>(smem);
+  Stage<T, D> st = carve_stage<T, D>(reinterpret_cast<unsigned char*>(tile + ntile), maxsub);
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(s.rec);
+  const int T0 = g.T[0], T01 = g.T[0] * g.T[1];
+
+  for (;;) {
+    if (threadIdx.x == 0) s_sub = atomicAdd(work, 1);
+    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int sub = s_sub;
+    if (sub >= *s.nsub) break;
+    const int bin = s.sub_bin[sub], p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+
+    // fetch the tile (bin + halo) from the fine grid, wrapping periodically
+    int org[3];
+    tile_origin(g, bin, org);
+    const int nrows = ntile / T0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
+      const int t1 = row % g.T[1], t2 = row / g.T[1];
+      const long long gy = wrap_idx(org[1] + t1, g.n[1]);
+      const long long gz = wrap_idx(org[2] + t2, g.n[2]);
+      const C* grow = grid + (gz * g.n[1] + gy) * (long long)g.n[0];
+      for (int t0 = lane; t0 < T0; t0 += 32) tile[row * T0 + t0] = grow[wrap_idx(org[0] + t0, g.n[0])];
+    }
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) stage_point<T, D, W>(g, rec[p0 + q], q, st, hist);
+    bucket_order<T, D>(cnt, st, hist);
+
+    const int Q = (cnt + 31) >> 5;
+    for (int sl = threadIdx.x; sl < (Q << 5); sl += blockDim.x) {
+      const int pos = (sl & 31) * Q + (sl >> 5);
+      if (pos >= cnt) continue;
+      const int q = st.order[pos];
+      T k0[W];
+      int ts0, ts1 = 0, ts2 = 0;
+      point_weights<T, W>(st.v[q * D], g.B[0], kpar, ts0, k0);
+      T k1[(D > 1) ? W : 1];
+      T f2 = T(0);
+      int st2 = 0;
+      if constexpr (D > 1) point_weights<T, W>(st.v[q * D + 1], g.B[1], kpar, ts1, k1);
+      else k1[0] = T(1);
+      if constexpr (D > 2) {
+        T v2 = st.v[q * D + 2];
+        int il2 = min((int)v2, g.B[2] - 1);
+        f2 = v2 - T(il2);
+        st2 = stencil_step<W>(f2);
+        ts2 = il2 + st2;
+      }
+      const int base = ts0 + T0 * ts1 + T01 * ts2;
+      constexpr int W1 = (D > 1) ? W : 1;
+      constexpr int W2 = (D > 2) ? W : 1;
+      T ar = T(0), ai = T(0);
+#pragma unroll 1
+      for (int l2 = 0; l2 < W2; ++l2) {
+        T br = T(0), bi = T(0);
+#pragma unroll
+        for (int l1 = 0; l1 < W1; ++l1) {
+          const C* rowp = tile + base + l1 * T0 + l2 * T01;
+          T sr = T(0), si = T(0);
+#pragma unroll
+          for (int l0 = 0; l0 < W; ++l0) {
+            const C gv = rowp[l0];
+            sr = fma(gv.x, k0[l0], sr);
+            si = fma(gv.y, k0[l0], si);
+          }
+          br = fma(sr, k1[l1], br);
+          bi = fma(si, k1[l1], bi);
+        }
+        T k2 = T(1);
+        if constexpr (D > 2) k2 = es_eval(node_z<W>(l2, st2, f2), kpar);
+        ar = fma(br, k2, ar);
+        ai = fma(bi, k2, ai);
+      }
+      C out;
+      out.x = ar;
+      out.y = ai;
+      c[st.idx[q]] = out;
+    }
+    __syncthreads();
+  }
+}
+
+// shared-memory bytes of each kernel
+template <typename T, int D>
+inline size_t spread_bytes(const Geom& g) {
+  using I = typename Fixed<T>::I;
+  return 2 * (size_t)g.ntile * sizeof(I) + (size_t)g.maxsub * sizeof(typename Traits<T>::C) +
+         stage_bytes<T, D>(g.maxsub);
+}
+template <typename T, int D>
+inline size_t interp_bytes(const Geom& g) {
+  return (size_t)g.ntile * sizeof(typename Traits<T>::C) + stage_bytes<T, D>(g.maxsub);
+}
+
+template <typename T>
+inline T kernel_param(double beta);
+template <>
+inline float kernel_param<float>(double beta) {
+  return (float)(beta * 1.4426950408889634073599246810019);
+}
+template <>
+inline double kernel_param<double>(double beta) {
+  return beta;
+}
+
+template <typename T, int D, int W>
+cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* c, void* grid,
+                       int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only) {
+  auto kern = k_spread<T, D, W>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.threads, cfg.smem);
+    if (e != cudaSuccess) return e;
+    const_cast<LaunchCfg&>(cfg).blocks = nb;  // blocks per SM; caller scales
+    return cudaSuccess;
+  }
+  kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
+      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
+      reinterpret_cast<typename Traits<T>::C*>(grid), work);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int W>
+cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* grid, void* c,
+                       int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only) {
+  auto kern = k_interp<T, D, W>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.threads, cfg.smem);
+    if (e != cudaSuccess) return e;
+    const_cast<LaunchCfg&>(cfg).blocks = nb;
+    return cudaSuccess;
+  }
+  kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
+      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
+      reinterpret_cast<typename Traits<T>::C*>(c), work);
+  return cudaGetLastError();
+}
+
+// w -> template dispatch for one (precision, dimension)
+#define NUFFT_W_CASES(FN, T, D)                                             \
+  switch (g.w) {                                                            \
+    case 2: return FN<T, D, 2>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 3: return FN<T, D, 3>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 4: return FN<T, D, 4>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 5: return FN<T, D, 5>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 6: return FN<T, D, 6>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 7: return FN<T, D, 7>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 8: return FN<T, D, 8>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 9: return FN<T, D, 9>(g, beta, s, a, b, work, cfg, st, conf);      \
+    case 10: return FN<T, D, 10>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 11: return FN<T, D, 11>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 12: return FN<T, D, 12>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 13: return FN<T, D, 13>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 14: return FN<T, D, 14>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 15: return FN<T, D, 15>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 16: return FN<T, D, 16>(g, beta, s, a, b, work, cfg, st, conf);    \
+    default: return cudaErrorInvalidValue;                                  \
+  }
+
+#define NUFFT_DEFINE_SI(P, T, D)                                                                   \
+  cudaError_t spread_##P##_d##D(const Geom& g, double beta, const Sorted& s, const void* a,       \
+                                void* b, int* work, const LaunchCfg& cfg, cudaStream_t st,         \
+                                bool conf) {                                                       \
+    NUFFT_W_CASES(run_spread, T, D)                                                                \
+  }                                                                                                \
+  cudaError_t interp_##P##_d##D(const Geom& g, double beta, const Sorted& s, const void* a,       \
+                                void* b, int* work, const LaunchCfg& cfg, cudaStream_t st,         \
+                                bool conf) {                                                       \
+    NUFFT_W_CASES(run_interp, T, D)                                                                \
+  }
+
+}  // namespace nufft

@@ -1,0 +1,90 @@
+"""The C-ABI library loads, exports every symbol the header declares, and its
+host-only parameter logic agrees with the oracle's (independent code).  No
+device call is made."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nufft_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1808_06736_gb300 import build
+    build.build()
+    import paper_1808_06736_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nufft_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    import ctypes
+    names = _declared()
+    assert len(names) >= 12
+    so = ctypes.CDLL(lib.library_path())
+    for n in names:
+        assert hasattr(so, n), n
+
+
+def test_strerror_and_defaults(lib):
+    assert lib.nufft_strerror(0) == "success"
+    assert "argument" in lib.nufft_strerror(-1)
+    o = lib.nufft_default_opts()
+    assert o.debug == 0 and o.modeord == 0 and o.bin_size[0] == 0
+
+
+def test_choose_params_matches_oracle(lib, oracle_mod):
+    for eps in [0.5, 1e-2, 1e-3, 1e-5, 1e-6, 1e-9, 1e-12, 1e-15, 1e-18]:
+        for Ns in ([1000], [24, 17], [256, 256, 256], [1, 3, 7]):
+            st, w, beta, n = lib.nufft_choose_params(len(Ns), Ns, eps, lib.NUFFT_C128)
+            wo, bo, no = oracle_mod.choose_params(eps, Ns)
+            assert (w, n) == (wo, no), (eps, Ns)
+            assert beta == pytest.approx(bo, rel=1e-15)
+            assert st == (1 if eps < 1e-15 else 0)
+    st, *_ = lib.nufft_choose_params(3, [8, 8, 8], 1e-7, lib.NUFFT_C64)
+    assert st == 1  # fp32 cannot deliver 1e-7
+
+
+def test_choose_params_rejects_bad_args(lib):
+    assert lib.nufft_choose_params(4, [8] * 3, 1e-6)[0] == -1
+    assert lib.nufft_choose_params(2, [8, 0], 1e-6)[0] == -1
+    assert lib.nufft_choose_params(1, [8], 0.0)[0] == -1
+    assert lib.nufft_choose_params(1, [8], float("nan"))[0] == -1
+
+
+def test_next235_matches_oracle(lib, oracle_mod):
+    for m in list(range(1, 400)) + [1000, 1023, 2047, 5001, 123457]:
+        assert lib.nufft_next235(m) == oracle_mod.next235(m)
+    assert lib.nufft_next235(0) == -1
+
+
+@pytest.mark.parametrize("w", [2, 4, 6, 7, 10, 13, 16])
+@pytest.mark.parametrize("N,n", [(1000, 2000), (255, 512), (7, 20), (3000, 6000)])
+def test_correction_factors_match_oracle(lib, oracle_mod, w, N, n):
+    """Library: Newton GL nodes + phase winding.  Oracle: numpy leggauss + direct cosines."""
+    beta = 2.30 * w
+    st, p = lib.nufft_correction_factors(N, n, w, beta)
+    assert st == 0
+    ref = oracle_mod.correction_factors(N, n, w, beta)
+    np.testing.assert_allclose(np.array(p), ref, rtol=1e-12, atol=0)
+
+
+def test_make_plan_validates_before_device_use(lib):
+    # argument errors are reported without touching a device
+    assert lib.nufft_makeplan(3, 1, [8], 1, 1, 1e-6, 1, None, None)[0] == -1
+    assert lib.nufft_makeplan(1, 1, [8], 0, 1, 1e-6, 1, None, None)[0] == -1
+    assert lib.nufft_makeplan(1, 1, [8], 1, 0, 1e-6, 1, None, None)[0] == -1
+    assert lib.nufft_makeplan(1, 1, [8], 1, 1, -1.0, 1, None, None)[0] == -1
+    assert lib.nufft_makeplan(1, 1, [8], 1, 1, 1e-6, 3, None, None)[0] == -1
+    assert lib.nufft_setpts(None, 10, 0, 0, 0) == -1
+    assert lib.nufft_execute(None, 0, 0) == -1
+    assert lib.nufft_destroy(None) == 0

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path against the CPU oracle on the same seeded inputs.
+
+Two bars, element by element over the whole output vector:
+  * against O1 (the exact sums Eq. (1)/(2)): relative l2 error <= 10 eps, the
+    acceptance bar of the method (eps >= 1e-5 in fp32, >= 1e-11 in fp64);
+  * against O2 (the plain ES algorithm at the same w, beta, n): the two differ
+    only by rounding, so the bar is a rounding budget: TOL_SAME below.
+Sizes span several bins and tiles with ragged tails (N_i not multiples of the
+bin extents, fine grids with factors 3 and 5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import nufft_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# Rounding budget GPU vs O2 at identical parameters (relative l2).  fp32: the
+# fold is accurate to ~1e-7 cells, kernel values to a few ulp, fixed-point
+# spreading rounds each contribution to max|c| 2^-22, and the fp32 FFT adds
+# ~log2(n) ulp; together a few 1e-6, budget 3e-5.  fp64: the same chain at
+# 2^-52 gives ~1e-14, budget 1e-12.
+TOL_SAME = {np.complex64: 3e-5, np.complex128: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_06736_gb300 import build
+    build.build()
+    import paper_1808_06736_gb300 as p
+    return p
+
+
+def gpu_transform(pkg, type_, Ns, xs, data, eps, isign, cdtype, **opts):
+    import torch
+    dev = torch.device("cuda:0")
+    tdt = torch.complex64 if cdtype == np.complex64 else torch.complex128
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    p = pkg.Plan(type_, Ns, eps=eps, isign=isign, dtype=tdt, device=dev, **opts)
+    p.setpts(*[torch.from_numpy(np.ascontiguousarray(v, dtype=rdt)).to(dev) for v in xs])
+    out = p.execute(torch.from_numpy(np.ascontiguousarray(data, dtype=cdtype)).to(dev))
+    res = out.cpu().numpy().reshape(p.n_trans, -1)
+    st = p.status()
+    info = p.info
+    p.close()
+    assert st == 0, st
+    return res, info
+
+
+def case_inputs(d, Ns, M, kind, cdtype, seed):
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    xs = I.points(seed, M, d, kind=kind, dtype=rdt)
+    c = I.complex_normal(seed + 1, M, dtype=cdtype)
+    f = I.complex_normal(seed + 2, int(np.prod(Ns)), dtype=cdtype)
+    return xs, c, f
+
+
+SIZES = {1: ([1000], 6000), 2: ([70, 45], 20000), 3: ([20, 18, 14], 30000)}
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex64, 1e-3), (np.complex128, 1e-9),
+                                        (np.complex128, 1e-12)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_parity_type1_type2(pkg, oracle_mod, cdtype, eps, d, kind):
+    Ns, M = SIZES[d]
+    xs, c, f = case_inputs(d, Ns, M, kind, cdtype, seed=1000 + 10 * d)
+    x64 = [v.astype(np.float64) for v in xs]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    g1, info = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype)
+    assert info["w"] == w and info["n"] == ns
+    g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype)
+    o2_1 = oracle_mod.type1(x64, c, 1, Ns, w=w, beta=beta, ns=ns)
+    o2_2 = oracle_mod.type2(x64, f, -1, Ns, w=w, beta=beta, ns=ns)
+    o1_1 = oracle_mod.direct_type1(x64, c, 1, Ns)
+    o1_2 = oracle_mod.direct_type2(x64, f, -1, Ns)
+    tol = TOL_SAME[cdtype]
+    assert oracle_mod.rel_l2(g1[0], o2_1) <= tol
+    assert oracle_mod.rel_l2(g2[0], o2_2) <= tol
+    assert oracle_mod.rel_l2(g1[0], o1_1) <= 10 * eps
+    assert oracle_mod.rel_l2(g2[0], o1_2) <= 10 * eps
+
+
+@pytest.mark.parametrize("cdtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_adjoint_on_gpu(pkg, cdtype, d):
+    """Sec. 4.1: <F1_s c, f> = <c, F2_{-s} f> holds to rounding for the discrete algorithm."""
+    Ns, M = SIZES[d]
+    xs, c, f = case_inputs(d, Ns, M, "uniform", cdtype, seed=2000 + d)
+    eps = 1e-5 if cdtype == np.complex64 else 1e-10
+    F1c, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype)
+    F2f, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype)
+    a = np.vdot(f.astype(np.complex128), F1c[0].astype(np.complex128))
+    b = np.vdot(F2f[0].astype(np.complex128), c.astype(np.complex128))
+    scale = np.linalg.norm(f) * np.linalg.norm(F1c[0])
+    assert abs(a - b) <= (1e-5 if cdtype == np.complex64 else 1e-12) * scale
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex128, 1e-11)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_edge_points(pkg, oracle_mod, cdtype, eps, d):
+    """Points at -pi, 0, just below pi, on grid nodes and bin edges, and in [-3 pi, 3 pi]."""
+    Ns = [16, 12, 10][:d]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    xs, M = I.edge_points(d, ns, dtype=rdt)
+    c = I.complex_normal(5, M, dtype=cdtype)
+    f = I.complex_normal(6, int(np.prod(Ns)), dtype=cdtype)
+    x64 = [v.astype(np.float64) for v in xs]
+    g1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype)
+    g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype)
+    assert oracle_mod.rel_l2(g1[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= 10 * eps
+    assert oracle_mod.rel_l2(g2[0], oracle_mod.direct_type2(x64, f, -1, Ns)) <= 10 * eps
+
+
+def test_1d_type1_fp64_full_direct_sum(pkg, oracle_mod):
+    """1D type 1, complex128: N = 1000, M = 1000, eps = 1e-9, isign = +1, against the full O(NM) sum."""
+    xs = I.points(1001, 1000, 1, dtype=np.float64)
+    c = I.complex_normal(1002, 1000, dtype=np.complex128)
+    g, _ = gpu_transform(pkg, 1, [1000], xs, c, 1e-9, 1, np.complex128)
+    assert oracle_mod.rel_l2(g[0], oracle_mod.direct_type1(xs, c, 1, [1000])) <= 1e-8
+
+
+@pytest.mark.parametrize("type_", [1, 2])
+def test_zero_points(pkg, type_):
+    import torch
+    p = pkg.Plan(type_, [8, 6], eps=1e-6, dtype=torch.complex64)
+    p.setpts(torch.zeros(0, device="cuda"), torch.zeros(0, device="cuda"))
+    if type_ == 1:
+        out = p.execute(torch.zeros(0, dtype=torch.complex64, device="cuda"))
+        assert out.shape == (1, 6, 8) and float(out.abs().max()) == 0.0
+    else:
+        out = p.execute(torch.ones(48, dtype=torch.complex64, device="cuda"))
+        assert out.shape == (1, 0)
+    assert p.status() == 0
+    p.close()
+
+
+def test_modeord_and_ntransf(pkg, oracle_mod):
+    """FFT mode order (modeord = 1) and three vectors per execute."""
+    Ns = [12, 9]
+    M = 500
+    xs = I.points(77, M, 2, dtype=np.float64)
+    cs = np.stack([I.complex_normal(78 + t, M) for t in range(3)])
+    g, _ = gpu_transform(pkg, 1, Ns, xs, cs, 1e-10, -1, np.complex128, modeord=1, n_trans=3)
+    k = oracle_mod.mode_list(Ns)
+    for t in range(3):
+        ref = oracle_mod.direct_type1(xs, cs[t], -1, Ns)
+        # position of mode k in FFT order: (k mod N) per dimension
+        pos = np.mod(k[:, 0], Ns[0]) + Ns[0] * np.mod(k[:, 1], Ns[1])
+        got = np.empty_like(ref)
+        got[:] = g[t][pos]
+        assert oracle_mod.rel_l2(got, ref) <= 1e-9
+    # type 2 with three coefficient vectors in FFT order
+    fs = np.stack([I.complex_normal(90 + t, 108) for t in range(3)])
+    g2, _ = gpu_transform(pkg, 2, Ns, xs, fs, 1e-10, 1, np.complex128, modeord=1, n_trans=3)
+    for t in range(3):
+        f_inc = np.empty(108, dtype=np.complex128)
+        pos = np.mod(k[:, 0], Ns[0]) + Ns[0] * np.mod(k[:, 1], Ns[1])
+        f_inc[:] = fs[t][pos]
+        ref = oracle_mod.direct_type2(xs, f_inc, 1, Ns)
+        assert oracle_mod.rel_l2(g2[t], ref) <= 1e-9
+
+
+def test_chkbnds_reports_out_of_range(pkg):
+    import torch
+    p = pkg.Plan(1, [16], eps=1e-6, dtype=torch.complex64, chkbnds=1)
+    x = torch.tensor([0.0, 1.0, 10.0, -2.0], device="cuda")
+    p.setpts(x)
+    p.execute(torch.ones(4, dtype=torch.complex64, device="cuda"))
+    assert p.status() == -2
+    assert p.status() == 0  # cleared
+    p.setpts(torch.tensor([0.0, 9.4, -9.4], device="cuda"))
+    p.execute(torch.ones(3, dtype=torch.complex64, device="cuda"))
+    assert p.status() == 0
+    p.close()
+
+
+def test_single_point_closed_form(pkg):
+    """M = 1, c = 1 at x0: f_k = exp(i k.x0) (Eq. (1)); at x0 = 0 every f_k = 1."""
+    import torch
+    Ns = [10, 8, 6]
+    for x0 in ([0.0, 0.0, 0.0], [0.7, -2.1, 3.0]):
+        xs = [np.array([v]) for v in x0]
+        g, _ = gpu_transform(pkg, 1, Ns, xs, np.array([1.0 + 0j]), 1e-12, 1, np.complex128)
+        k3, k2, k1 = np.meshgrid(*[np.arange(n) - n // 2 for n in reversed(Ns)], indexing="ij")
+        ref = np.exp(1j * (k1 * x0[0] + k2 * x0[1] + k3 * x0[2])).ravel()
+        assert np.max(np.abs(g[0] - ref)) < 1e-10
+
+
+def test_small_bins_and_subproblems(pkg, oracle_mod):
+    """Forced small bins and subproblems: many subproblems per bin, the same result."""
+    Ns = [32, 30, 28]
+    xs, c, f = case_inputs(3, Ns, 20000, "clustered", np.complex64, seed=3000)
+    x64 = [v.astype(np.float64) for v in xs]
+    a, info = gpu_transform(pkg, 1, Ns, xs, c, 1e-5, 1, np.complex64, bin_size=(8, 4, 4), max_subprob=64)
+    assert info["bins"] == [8, 4, 4]
+    b, _ = gpu_transform(pkg, 2, Ns, xs, f, 1e-5, -1, np.complex64, bin_size=(8, 4, 4), max_subprob=64)
+    assert oracle_mod.rel_l2(a[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= 1e-4
+    assert oracle_mod.rel_l2(b[0], oracle_mod.direct_type2(x64, f, -1, Ns)) <= 1e-4
