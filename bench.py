@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: type-1 / type-2 NU points per second, 3D, complex64, eps = 1e-5.
+
+Workload (default): N = 256^3 modes (fine grid 512^3), M = 1e8 points iid
+uniform in [-pi, pi)^3, strengths / coefficients with re, im iid N(0, 1),
+eps = 1e-5 (w = 6, beta = 13.8).  One step is the whole hot path on one
+batch: setpts + type-1 execute on one plan (bin, spread, FFT, deconvolve) and
+setpts + type-2 execute on another (bin, pre-correct, FFT, interpolate), all
+on the same points.  value = 2 M / step time (each transform counts its M
+points).  Inputs (1.2 GB of coordinates, 1 GB fine grids) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+Arms:
+  default            the CUDA library, inputs resident in HBM; the JSON line adds
+                     e2e (host buffers, copies inside the timed region), the
+                     roofline of the dominant kernel, clocks and a bounded CPU
+                     baseline (the oracle)
+  --impl reference   the CPU oracle, as it stands, on a bounded sample
+N > 1 GPUs (torchrun): independent replicas, one per rank (the path has no
+exchange step); value sums the ranks' points over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "type1/2 NU points/s at eps=1e-5 (3D, fp32)"
+UNIT = "NU points/s"
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--M", type=int, default=100_000_000)
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--eps", type=float, default=1e-5)
+    ap.add_argument("--kind", default="uniform", choices=["uniform", "clustered"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=300_000)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CUDA arm
+def algorithmic_units(d, w):
+    """Per NU point, spread or interp: flops (complex x real accumulate, tensor
+    weights, kernel arguments) and HBM bytes (record, index, strength, grid
+    amortised separately)."""
+    flops = 4 * w ** d + 2 * w ** (d - 1) + 10 * w * d
+    return flops
+
+
+def run_cuda(args, ws, rank, local):
+    import torch
+    import numpy as np
+
+    import nufft_inputs as I
+    import paper_1808_06736_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    d, N, M, eps = 3, args.N, args.M, args.eps
+    Ns = [N] * d
+    seed = 1000 + 2 + 10 * (1 if args.kind == "clustered" else 0) + rank
+    xs = I.torch_points(seed, M, d, args.kind, dev, torch.float32)
+    c = I.torch_complex_normal(seed + 1, M, dev, torch.complex64)
+    f = I.torch_complex_normal(seed + 2, N ** d, dev, torch.complex64)
+    stream = torch.cuda.current_stream(dev)
+    p1 = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=torch.complex64, device=dev, debug=1)
+    p2 = pkg.Plan(2, Ns, eps=eps, isign=-1, dtype=torch.complex64, device=dev, debug=1)
+    fout = torch.empty((1,) + tuple(Ns), dtype=torch.complex64, device=dev)
+    cout = torch.empty((1, M), dtype=torch.complex64, device=dev)
+    slots = {k: [] for k in ("fold", "scan", "scatter", "spread", "fft1", "deconv", "precorrect", "fft2",
+                             "interp")}
+
+    def step(record):
+        p1.setpts(*xs)
+        if record:
+            t = p1.timings()
+        p1.execute(c, out=fout)
+        if record:
+            t1 = p1.timings()
+        p2.setpts(*xs)
+        p2.execute(f, out=cout)
+        if record:
+            t2 = p2.timings()
+            slots["fold"].append(t[0]); slots["scan"].append(t[1]); slots["scatter"].append(t[2])
+            slots["spread"].append(t1[3]); slots["fft1"].append(t1[4]); slots["deconv"].append(t1[5])
+            slots["precorrect"].append(t2[3]); slots["fft2"].append(t2[4]); slots["interp"].append(t2[5])
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(False)
+    assert p1.status() == 0 and p2.status() == 0
+    # per-step kernel timings (debug events on the plans' stream), separate pass
+    for _ in range(max(3, min(args.steps, 5))):
+        step(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(False)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = (p1.status(), p2.status())
+    if st != (0, 0):
+        raise RuntimeError("device status %s" % (st,))
+    ms_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * 2 * M / (ms_max * 1e-3)
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hx = [v.cpu().pin_memory() for v in xs]
+        hc = c.cpu().pin_memory()
+        hf = f.cpu().pin_memory()
+        hfo = torch.empty(fout.shape, dtype=torch.complex64).pin_memory()
+        hco = torch.empty(cout.shape, dtype=torch.complex64).pin_memory()
+        dx = [torch.empty_like(v) for v in xs]
+        dc, df = torch.empty_like(c), torch.empty_like(f)
+
+        def step_e2e():
+            for a, b in zip(dx, hx):
+                a.copy_(b, non_blocking=True)
+            dc.copy_(hc, non_blocking=True)
+            df.copy_(hf, non_blocking=True)
+            p1.setpts(*dx)
+            p1.execute(dc, out=fout)
+            p2.setpts(*dx)
+            p2.execute(df, out=cout)
+            hfo.copy_(fout, non_blocking=True)
+            hco.copy_(cout, non_blocking=True)
+
+        for _ in range(2):
+            step_e2e()
+        barrier()
+        e0.record(stream)
+        ke = max(3, min(args.steps, 5))
+        for _ in range(ke):
+            step_e2e()
+        e1.record(stream)
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / ke
+        h2d = sum(v.numel() * v.element_size() for v in hx) + hc.numel() * 8 + hf.numel() * 8
+        d2h = hfo.numel() * 8 + hco.numel() * 8
+        e2e = {"value": ws * 2 * M / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel
+    med = {k: statistics.median(v) for k, v in slots.items()}
+    w = p1.info["w"]
+    dominant = max(("spread", "interp"), key=lambda k: med[k])
+    flops = algorithmic_units(d, w) * M
+    achieved = flops / (med[dominant] * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12  # max SM clock 2070 MHz
+    roof = {"bound": "alu", "kernel": "k_%s (3D, w=%d, fp32)" % (dominant, w), "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop x 2.07 GHz" % (sms, FP32_LANES_PER_SM),
+            "algorithmic_flops_per_point": algorithmic_units(d, w)}
+    kernels_ms = {k: round(v, 4) for k, v in med.items()}
+    p1.close()
+    p2.close()
+    launches = args.steps * 12  # per step: 4 setpts kernels x 2 plans + spread, deconv, precorrect, interp
+    return {"value": value, "ms": ms_max, "e2e": e2e, "roofline": roof, "kernels_ms": kernels_ms,
+            "clocks": clk, "gpu_launches": launches, "w": w}
+
+
+# -------------------------------------------------------------- oracle arm
+def oracle_sample(args, M_sample, reps=1):
+    """Time the oracle (O2) on the workload: spread and interp on a random
+    sample of M_sample points (their cost is linear in M), the FFTs and the
+    correction steps on the full fine grid.  Returns the extrapolated
+    full-workload step time and the parts."""
+    import numpy as np
+
+    import nufft_inputs as I
+    import oracle
+
+    d, N, M, eps = 3, args.N, args.M, args.eps
+    Ns = [N] * d
+    w, beta, ns = oracle.choose_params(eps, Ns)
+    xs = I.points(4242, M_sample, d, kind=args.kind)
+    c = I.complex_normal(4243, M_sample)
+    f = I.complex_normal(4244, N ** d)
+    t_pts = t_fixed = 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        b = oracle.spread(xs, c, ns, w, beta)
+        t1 = time.perf_counter()
+        fk = oracle.deconvolve(oracle.dft(b, 1), Ns, ns, w, beta)
+        del b
+        b2 = oracle.dft(oracle.precorrect(f, Ns, ns, w, beta), -1)
+        t2 = time.perf_counter()
+        cc = oracle.interp(xs, b2, ns, w, beta)
+        t3 = time.perf_counter()
+        del b2, fk, cc
+        t_pts += (t1 - t0) + (t3 - t2)
+        t_fixed += t2 - t1
+    t_pts /= reps
+    t_fixed /= reps
+    full = t_fixed + t_pts * (M / M_sample)
+    return full, t_pts, t_fixed, oracle.dft.__module__, len(os.sched_getaffinity(0))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    Ms = args.cpu_sample
+    steps = []
+    for i in range(args.warmup + args.steps):
+        full, t_pts, t_fixed, _, cores = oracle_sample(args, Ms)
+        if i >= args.warmup:
+            steps.append((full, t_pts, t_fixed))
+    full = statistics.median(s[0] for s in steps)
+    value = 2 * args.M / full
+    sample = ("oracle O2 (fp64, C loops + scipy FFT): spread+interp on %d of the %d points, timed and scaled "
+              "linearly in M; FFTs and corrections on the full %d^3 fine grid" % (Ms, args.M, 2 * args.N))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(args):
+    return {"workload": "3D type 1 + type 2, N=%d^3 modes (fine grid %d^3), M=%d %s points, complex64, eps=%g"
+                        % (args.N, 2 * args.N, args.M, args.kind, args.eps),
+            "modes": [args.N] * 3, "fine_grid": [2 * args.N] * 3, "M": args.M, "points": args.kind,
+            "eps": args.eps, "step": "setpts+type1 and setpts+type2 on the same points; value = 2M/step",
+            "l2": "inputs larger than L2 (1.2 GB coordinates, 1 GB fine grids), no flush",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args)
+    r = run_cuda(args, ws, rank, local)
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu:
+        full, t_pts, t_fixed, _, cores = oracle_sample(args, args.cpu_sample)
+        cpu = {"value": 2 * args.M / full, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "spread+interp on %d of %d points (%.2f s, scaled linearly in M), FFT+correction on "
+                         "the full grid (%.2f s, scipy FFT on %d threads; C loops single-threaded)"
+                         % (args.cpu_sample, args.M, t_pts, t_fixed, cores)}
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args),
+            "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
+            "gpu_launches": r["gpu_launches"], "kernels_ms": r["kernels_ms"]}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

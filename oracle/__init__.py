@@ -286,6 +286,19 @@ def _outer_correction(Ns, ns, w, beta):
     return p
 
 
+def deconvolve(bh: np.ndarray, Ns, ns, w: int, beta: float) -> np.ndarray:
+    """Type-1 step 3, Eq. (pb1) with Eq. (pk): f_k = p_k b^_{k mod n} for k in I_N (mode order)."""
+    return (bh[_truncation_index(Ns, ns)] * _outer_correction(Ns, ns, w, beta)).ravel()
+
+
+def precorrect(f, Ns, ns, w: int, beta: float) -> np.ndarray:
+    """Type-2 step 1 (Sec. 3.2): b^_{k mod n} = p_k f_k on I_N, zero elsewhere on the fine grid."""
+    f = _cplx(f).reshape(tuple(reversed([int(v) for v in Ns])))
+    bh = np.zeros(tuple(reversed([int(v) for v in ns])), dtype=np.complex128)
+    bh[_truncation_index(Ns, ns)] = f * _outer_correction(Ns, ns, w, beta)
+    return bh
+
+
 def type1(xs, c, isign: int, Ns, eps: float | None = None, w: int | None = None,
           beta: float | None = None, ns=None) -> np.ndarray:
     """O2 type 1 (Sec. 3.1): spread Eq. (bl), DFT Eq. (dft1) with sign isign, truncate and
@@ -294,9 +307,7 @@ def type1(xs, c, isign: int, Ns, eps: float | None = None, w: int | None = None,
     if w is None:
         w, beta, ns = choose_params(eps, Ns)
     b = spread(xs, c, ns, w, beta)
-    bh = dft(b, isign)
-    f = bh[_truncation_index(Ns, ns)] * _outer_correction(Ns, ns, w, beta)
-    return f.ravel()
+    return deconvolve(dft(b, isign), Ns, ns, w, beta)
 
 
 def type2(xs, f, isign: int, Ns, eps: float | None = None, w: int | None = None,
@@ -306,8 +317,5 @@ def type2(xs, f, isign: int, Ns, eps: float | None = None, w: int | None = None,
     Ns = [int(v) for v in Ns]
     if w is None:
         w, beta, ns = choose_params(eps, Ns)
-    f = _cplx(f).reshape(tuple(reversed(Ns)))
-    bh = np.zeros(tuple(reversed([int(v) for v in ns])), dtype=np.complex128)
-    bh[_truncation_index(Ns, ns)] = f * _outer_correction(Ns, ns, w, beta)
-    b = dft(bh, isign)
+    b = dft(precorrect(f, Ns, ns, w, beta), isign)
     return interp(xs, b, ns, w, beta)

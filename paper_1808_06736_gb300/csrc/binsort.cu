@@ -5,11 +5,12 @@
 // sum into breakpoints, write each point into its box, no order inside a box
 // (Sec. 5.1).  Sorted points are then grouped into subproblems of bounded
 // size (Sec. 5.2).  Here:
-//   k_fold_count  per point: fold, bin id, rank in its bin (global atomicAdd)
-//   k_scan        one block: bin breakpoints + subproblem breakpoints
+//   k_fold_count  per point: fold, bin id, count (global atomic reduction)
+//   k_scan        one block: bin breakpoints (also the scatter cursors) and
+//                 subproblem breakpoints
 //   k_sublist     per bin: its subproblems (bin, first record, count)
 //   k_scatter     per point: folded coordinates relative to the bin origin,
-//                 written as one record at breakpoint + rank
+//                 written as one record at the bin's cursor (atomicAdd)
 #include <cmath>
 
 #include "nufft_internal.cuh"
@@ -90,8 +91,7 @@ __device__ __forceinline__ T coord(int dim, int j, const T* x, const T* y, const
 template <typename T>
 __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict__ y,
                              const T* __restrict__ z, Geom g, FoldConst fc, int chk,
-                             int* __restrict__ bin_count, int* __restrict__ pt_rank,
-                             int* __restrict__ err) {
+                             int* __restrict__ bin_count, int* __restrict__ err) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
     int bin = 0, stride = 1;
     bool bad = false;
@@ -108,67 +108,63 @@ __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict
       }
     }
     if (chk && bad) atomicCAS(err, 0, NUFFT_ERR_OUT_OF_RANGE);
-    pt_rank[j] = atomicAdd(&bin_count[bin], 1);
+    atomicAdd(&bin_count[bin], 1);  // result unused: a fire-and-forget reduction
   }
 }
 
-// Exclusive scans of the bin counts and of the per-bin subproblem counts, in
-// one block: each thread owns a contiguous chunk.
-__global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, const int* __restrict__ cnt,
-                                               int* __restrict__ start, int* __restrict__ sub_first,
-                                               int* __restrict__ nsub) {
-  __shared__ long long wsum_p[32], wsum_s[32];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int chunk = (nbins + nt - 1) / nt;
-  const int b0 = min(nbins, tid * chunk), b1 = min(nbins, b0 + chunk);
-  long long sp = 0, ss = 0;
-  for (int b = b0; b < b1; ++b) {
-    int c = cnt[b];
-    sp += c;
-    ss += (c + maxsub - 1) / maxsub;
-  }
-  // block exclusive scan of (sp, ss)
-  const int lane = tid & 31, wid = tid >> 5;
-  long long ip = sp, is = ss;
+// Exclusive scans of the bin counts (-> breakpoints and scatter cursors) and
+// of the per-bin subproblem counts, in one block: the block walks the bins in
+// chunks of blockDim (coalesced), carrying the running totals.
+__device__ __forceinline__ int block_incl_scan(int v, int* wsum) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    long long tp = __shfl_up_sync(0xffffffffu, ip, o);
-    long long ts = __shfl_up_sync(0xffffffffu, is, o);
-    if (lane >= o) {
-      ip += tp;
-      is += ts;
-    }
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
   }
-  if (lane == 31) {
-    wsum_p[wid] = ip;
-    wsum_s[wid] = is;
-  }
+  if (lane == 31) wsum[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    long long vp = lane < (nt >> 5) ? wsum_p[lane] : 0, vs = lane < (nt >> 5) ? wsum_s[lane] : 0;
+    int u = lane < nw ? wsum[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      long long tp = __shfl_up_sync(0xffffffffu, vp, o);
-      long long ts = __shfl_up_sync(0xffffffffu, vs, o);
-      if (lane >= o) {
-        vp += tp;
-        vs += ts;
-      }
+      int t = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += t;
     }
-    wsum_p[lane] = vp;  // inclusive over warps
-    wsum_s[lane] = vs;
+    wsum[lane] = u;
   }
   __syncthreads();
-  long long basep = (ip - sp) + (wid > 0 ? wsum_p[wid - 1] : 0);
-  long long bases = (is - ss) + (wid > 0 ? wsum_s[wid - 1] : 0);
-  for (int b = b0; b < b1; ++b) {
-    int c = cnt[b];
-    start[b] = (int)basep;
-    sub_first[b] = (int)bases;
-    basep += c;
-    bases += (c + maxsub - 1) / maxsub;
+  int r = v + (wid > 0 ? wsum[wid - 1] : 0);
+  __syncthreads();  // wsum reused by the next call
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, const int* __restrict__ cnt,
+                                               int* __restrict__ start, int* __restrict__ cursor,
+                                               int* __restrict__ sub_first, int* __restrict__ nsub) {
+  __shared__ int wsum[32];
+  __shared__ int carry[2];
+  if (threadIdx.x == 0) carry[0] = carry[1] = 0;
+  __syncthreads();
+  for (int base = 0; base < nbins; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    const int c = b < nbins ? cnt[b] : 0;
+    const int sc = (c + maxsub - 1) / maxsub;
+    const int cp = carry[0], cs = carry[1];
+    const int ip = block_incl_scan(c, wsum);
+    const int is = block_incl_scan(sc, wsum);
+    if (b < nbins) {
+      start[b] = cp + ip - c;
+      cursor[b] = cp + ip - c;
+      sub_first[b] = cs + is - sc;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+      carry[0] = cp + ip;
+      carry[1] = cs + is;
+    }
+    __syncthreads();
   }
-  if (tid == nt - 1) *nsub = (int)bases;  // total number of subproblems
+  if (threadIdx.x == 0) *nsub = carry[1];
 }
 
 __global__ void k_sublist(int nbins, int maxsub, const int* __restrict__ cnt,
@@ -188,8 +184,7 @@ __global__ void k_sublist(int nbins, int maxsub, const int* __restrict__ cnt,
 
 template <typename T>
 __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ y,
-                          const T* __restrict__ z, Geom g, FoldConst fc,
-                          const int* __restrict__ pt_rank, const int* __restrict__ start,
+                          const T* __restrict__ z, Geom g, FoldConst fc, int* __restrict__ cursor,
                           typename Traits<T>::Rec* __restrict__ rec) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
     typename Traits<T>::Rec r;
@@ -208,7 +203,7 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
       }
     }
     r.idx = j;
-    rec[start[bin] + pt_rank[j]] = r;
+    rec[atomicAdd(&cursor[bin], 1)] = r;  // order inside a bin is arbitrary
   }
 }
 
@@ -226,7 +221,7 @@ int grid_for(int64_t work, int threads) {
 template <typename T>
 cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, const void* y,
                      const void* z, int chk, int* bin_count, int* bin_start, int* sub_first,
-                     int* pt_rank, void* rec, int* sub_bin, int* sub_pt0, int* sub_cnt, int* nsub,
+                     int* cursor, void* rec, int* sub_bin, int* sub_pt0, int* sub_cnt, int* nsub,
                      int* err, cudaStream_t st, cudaEvent_t* ev) {
   const T* xp = (const T*)x;
   const T* yp = g.d > 1 ? (const T*)y : xp;
@@ -235,18 +230,18 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
   if (ev) cudaEventRecord(ev[0], st);
   if ((e = cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)g.nbins, st)) != cudaSuccess) return e;
   if (M > 0) {
-    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, bin_count, pt_rank, err);
+    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, bin_count, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
-  k_scan<<<1, 1024, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start, sub_first, nsub);
+  k_scan<<<1, 1024, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start, cursor, sub_first, nsub);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_sublist<<<grid_for(g.nbins, 256), 256, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start,
                                                      sub_first, sub_bin, sub_pt0, sub_cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], st);
   if (M > 0) {
-    k_scatter<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, pt_rank, bin_start,
+    k_scatter<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, cursor,
                                                     (typename Traits<T>::Rec*)rec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -258,13 +253,13 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
 
 cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
-                          int* sub_first, int* /*pt_bin*/, int* pt_rank, void* rec, int* sub_bin,
+                          int* sub_first, int* cursor, void* rec, int* sub_bin,
                           int* sub_pt0, int* sub_cnt, int* nsub, int* err, cudaStream_t st,
                           cudaEvent_t* ev) {
   if (dbl)
-    return setpts_t<double>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, pt_rank,
+    return setpts_t<double>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
                             rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev);
-  return setpts_t<float>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, pt_rank,
+  return setpts_t<float>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
                          rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev);
 }
 

@@ -29,8 +29,9 @@ __global__ void k_deconv(ModeGeom m, const typename Traits<T>::C* __restrict__ g
                          typename Traits<T>::C* __restrict__ f, const T* __restrict__ p1,
                          const T* __restrict__ p2, const T* __restrict__ p3) {
   using C = typename Traits<T>::C;
-  for (int m3 = blockIdx.z; m3 < m.N[2]; m3 += gridDim.z)
-  for (int m2 = blockIdx.y; m2 < m.N[1]; m2 += gridDim.y) {
+  const int nrows = m.N[1] * m.N[2];
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+  const int m2 = row % m.N[1], m3 = row / m.N[1];
   const int k2 = pos_to_k(m2, m.N[1], m.modeord), k3 = pos_to_k(m3, m.N[2], m.modeord);
   const int l2 = k2 < 0 ? k2 + m.n[1] : k2, l3 = k3 < 0 ? k3 + m.n[2] : k3;
   const T p23 = p2[k2 + m.N[1] / 2] * p3[k3 + m.N[2] / 2];
@@ -54,8 +55,9 @@ __global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict
                              typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
                              const T* __restrict__ p2, const T* __restrict__ p3) {
   using C = typename Traits<T>::C;
-  for (int l3 = blockIdx.z; l3 < m.n[2]; l3 += gridDim.z)
-  for (int l2 = blockIdx.y; l2 < m.n[1]; l2 += gridDim.y) {
+  const int nrows = m.n[1] * m.n[2];
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+  const int l2 = row % m.n[1], l3 = row / m.n[1];
   // fine-grid index l <-> mode k = l (l < N - N/2) or l - n (l >= n - N/2)
   const int k2 = l2 < m.N[1] - m.N[1] / 2 ? l2 : l2 - m.n[1];
   const int k3 = l3 < m.N[2] - m.N[2] / 2 ? l3 : l3 - m.n[2];
@@ -83,10 +85,16 @@ __global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict
   }
 }
 
+// x: chunks of a row; y: rows (grid-stride), about 8 resident blocks per SM
 dim3 row_grid(int len, int rows, int slabs, int threads) {
   int bx = (len + threads - 1) / threads;
   if (bx > 65535) bx = 65535;
-  return dim3(bx, rows < 65535 ? rows : 65535, slabs < 65535 ? slabs : 65535);
+  long long r = (long long)rows * slabs;
+  int by = (int)((152LL * 8 + bx - 1) / bx);
+  if (by < 1) by = 1;
+  if (by > r) by = (int)r;
+  if (by > 65535) by = 65535;
+  return dim3(bx, by, 1);
 }
 
 template <typename T>

@@ -71,8 +71,8 @@ FoldConst make_fold_const(const Geom& g);
 // Enqueue the whole setpts pipeline.  Work arrays are owned by the plan.
 cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
-                          int* sub_first, int* pt_bin, int* pt_rank, void* rec, int* sub_bin,
-                          int* sub_pt0, int* sub_cnt, int* nsub, int* err, cudaStream_t st,
+                          int* sub_first, int* cursor, void* rec, int* sub_bin, int* sub_pt0,
+                          int* sub_cnt, int* nsub, int* err, cudaStream_t st,
                           cudaEvent_t* ev /* 4 events or nullptr */);
 
 // --- spread / interp (spread_interp_*.cu) --------------------------------------

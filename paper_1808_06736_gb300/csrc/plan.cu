@@ -39,10 +39,10 @@ struct nufft_plan_s {
   int* bin_count = nullptr;
   int* bin_start = nullptr;
   int* sub_first = nullptr;
+  int* cursor = nullptr;  // per-bin scatter cursors
   int* small = nullptr;  // [0] error word, [1] nsub, [2] work counter
   int64_t M = -1;
   int64_t Mcap = 0;
-  int* pt_rank = nullptr;
   void* rec = nullptr;
   int64_t subcap = 0;
   int* sub_bin = nullptr;
@@ -389,6 +389,7 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   if (dev_alloc(&p->bin_count, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
       dev_alloc(&p->bin_start, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
       dev_alloc(&p->sub_first, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
+      dev_alloc(&p->cursor, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
       dev_alloc(&p->small, sizeof(int) * 4) != cudaSuccess)
     return fail(p, NUFFT_ERR_ALLOC);
   if (cudaMemset(p->small, 0, sizeof(int) * 4) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
@@ -421,15 +422,11 @@ int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const vo
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
   const Geom& g = p->g;
   if (M > p->Mcap) {
-    cudaFree(p->pt_rank);
     cudaFree(p->rec);
-    p->pt_rank = nullptr;
     p->rec = nullptr;
     p->Mcap = 0;
     size_t rsz = p->dbl ? sizeof(RecD) : sizeof(RecF);
-    if (dev_alloc(&p->pt_rank, sizeof(int) * (size_t)M) != cudaSuccess ||
-        dev_alloc(&p->rec, rsz * (size_t)M) != cudaSuccess)
-      return NUFFT_ERR_ALLOC;
+    if (dev_alloc(&p->rec, rsz * (size_t)M) != cudaSuccess) return NUFFT_ERR_ALLOC;
     p->Mcap = M;
   }
   int64_t need = std::min<int64_t>(g.nbins, M) + M / g.maxsub + 1;
@@ -447,7 +444,7 @@ int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const vo
   }
   FoldConst fc = make_fold_const(g);
   cudaError_t e = launch_setpts(p->dbl, g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
-                                p->sub_first, nullptr, p->pt_rank, p->rec, p->sub_bin, p->sub_pt0,
+                                p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0,
                                 p->sub_cnt, p->small + 1, p->small + 0, p->stream,
                                 p->ev_ok ? p->ev : nullptr);
   if (e != cudaSuccess) return NUFFT_ERR_CUDA;
@@ -475,25 +472,26 @@ int nufft_execute(nufft_plan p, void* c, void* f) {
   for (int t = 0; t < p->ntransf; ++t) {
     char* ct = (char*)c + (size_t)t * (size_t)p->M * p->csize;
     char* ft = (char*)f + (size_t)t * (size_t)p->Ntot * p->csize;
-    if (ev && t == 0) cudaEventRecord(ev[0], p->stream);
     if (p->type == 1) {
       CUDA_TRY(cudaMemsetAsync(p->grid, 0, (size_t)p->ngrid * p->csize, p->stream));
+      if (ev && t == 0) cudaEventRecord(ev[0], p->stream);
       if (p->M > 0) {
         CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
         CUDA_TRY(launch_spread(p->dbl, g, p->beta, s, ct, p->grid, p->small + 2, p->spread_cfg, p->stream));
       }
     } else {
+      if (ev && t == 0) cudaEventRecord(ev[0], p->stream);
       CUDA_TRY(launch_precorrect(p->dbl, mg, ft, p->grid, p->pk[0], p->pk[1], p->pk[2], p->stream));
     }
     if (ev && t == 0) cudaEventRecord(ev[1], p->stream);
     cufftResult r = p->dbl ? cufftExecZ2Z(p->fft, (cufftDoubleComplex*)p->grid, (cufftDoubleComplex*)p->grid, dir)
                            : cufftExecC2C(p->fft, (cufftComplex*)p->grid, (cufftComplex*)p->grid, dir);
     if (r != CUFFT_SUCCESS) return NUFFT_ERR_CUFFT;
+    if (p->type == 2 && p->M > 0) CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
     if (ev && t == 0) cudaEventRecord(ev[2], p->stream);
     if (p->type == 1) {
       CUDA_TRY(launch_deconv(p->dbl, mg, p->grid, ft, p->pk[0], p->pk[1], p->pk[2], p->stream));
     } else if (p->M > 0) {
-      CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
       CUDA_TRY(launch_interp(p->dbl, g, p->beta, s, p->grid, ct, p->small + 2, p->interp_cfg, p->stream));
     }
     if (ev && t == 0) cudaEventRecord(ev[3], p->stream);
@@ -512,7 +510,7 @@ int nufft_destroy(nufft_plan p) {
   if (p->ev_ok)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(p->ev[i]);
   void* bufs[] = {p->grid, p->pk[0], p->pk[1], p->pk[2], p->bin_count, p->bin_start, p->sub_first,
-                  p->small, p->pt_rank, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
+                  p->cursor, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
   for (void* b : bufs)
     if (b) cudaFree(b);
   cudaSetDevice(dev);

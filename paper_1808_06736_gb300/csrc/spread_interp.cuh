@@ -4,10 +4,11 @@
 //
 // Per subproblem a block
 //   1. stages the subproblem's point records in shared memory,
-//   2. counting-sorts them by the shared-memory bank of their stencil corner
-//      ("residue" = tile index mod 32) so that the 32 lanes of a warp, which
-//      take points a fixed stride apart in that order, touch 32 different
-//      banks on every access of the w^d loop,
+//   2. orders them so that the 16 lanes of each half-warp hold points whose
+//      stencil corners sit in 16 different shared-memory bank groups
+//      ("residue" = tile index of the corner mod 16): points are bucketed by
+//      residue and dealt out round-robin over the buckets, so every access of
+//      the w^d loop is conflict-free while all buckets still hold points,
 //   3. spreads into / gathers from a shared-memory tile that covers the bin
 //      plus a halo of floor(w/2) cells below and ceil(w/2) above, so the hot
 //      loop never wraps indices (the paper pads its cuboids by w/2 for the
@@ -90,6 +91,19 @@ __device__ __forceinline__ void red_add(double2* p, double a, double b) {
   atomicAdd(&p->y, b);
 }
 
+// Asynchronous global -> shared copies of one grid element (Ampere-style
+// cp.async; 8-byte copies go through L1, 16-byte ones bypass it).
+__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ int wrap_idx(int x, int n) {
   if ((unsigned)x >= (unsigned)n) {
     x %= n;
@@ -98,14 +112,23 @@ __device__ __forceinline__ int wrap_idx(int x, int n) {
   return x;
 }
 
+// Points are dealt to lanes by the bank group of their stencil corner.
+// Interpolation reads 8-byte (float2) tile entries: 16 groups of 8 bytes
+// cover the 32 four-byte banks and a half-warp is served in one pass when its
+// 16 lanes touch 16 different groups (NRES = 16).  Spreading issues 4-byte
+// integer atomics on separate re / im planes: a warp is served in one pass
+// when its 32 lanes touch 32 different banks (NRES = 32).
+constexpr int NRES_INTERP = 16;
+constexpr int NRES_SPREAD = 32;
+
 // Shared-memory layout common to both kernels (after the tile).
 template <typename T, int D>
 struct Stage {
-  T* v;                 // [maxsub * D] coordinates relative to the bin origin
-  int* idx;             // [maxsub] caller index
-  unsigned short* res;  // [maxsub] bank residue of the stencil corner
-  unsigned short* rank; // [maxsub] rank within its residue bucket
-  unsigned short* order;// [maxsub] records in residue order
+  T* v;                  // [maxsub * D] coordinates relative to the bin origin
+  int* idx;              // [maxsub] caller index
+  unsigned short* res;   // [maxsub] bank group of the stencil corner
+  unsigned short* rank;  // [maxsub] rank within its group
+  unsigned short* order; // [maxsub] processing order
 };
 
 template <typename T, int D>
@@ -137,9 +160,9 @@ __device__ __forceinline__ void tile_origin(const Geom& g, int bin, int* org) {
   org[2] = b2 * g.B[2] - g.half;
 }
 
-// Load a record into the stage and bucket it by residue.  Returns nothing;
-// hist[] must be zero on entry.
-template <typename T, int D, int W>
+// Store a record in the stage and count it in its bank group.  hist[] must
+// be zero on entry.
+template <typename T, int D, int W, int NRES>
 __device__ __forceinline__ void stage_point(const Geom& g, const typename Traits<T>::Rec& r, int q,
                                             Stage<T, D>& st, int* hist) {
   int base = 0, stride = 1;
@@ -152,26 +175,28 @@ __device__ __forceinline__ void stage_point(const Geom& g, const typename Traits
     stride *= g.T[d];
   }
   st.idx[q] = r.idx;
-  int rr = base & 31;
+  int rr = base & (NRES - 1);
   st.res[q] = (unsigned short)rr;
   st.rank[q] = (unsigned short)atomicAdd(&hist[rr], 1);
 }
 
-// hist -> exclusive bucket starts (warp 0), then order[] (all threads).
-template <typename T, int D>
-__device__ __forceinline__ void bucket_order(int cnt, Stage<T, D>& st, int* hist) {
+// Round-robin order over the bank groups: round r takes the r-th point of
+// every group that has more than r points, groups in increasing order.  The
+// point of group b with rank r lands at
+//   sum_g min(size_g, r) + #{g < b : size_g > r}.
+template <typename T, int D, int NRES>
+__device__ __forceinline__ void bucket_order(int cnt, Stage<T, D>& st, const int* hist) {
   __syncthreads();
-  if (threadIdx.x < 32) {
-    int v = hist[threadIdx.x], inc = v;
+  int sz[NRES];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (threadIdx.x >= o) inc += t;
-    }
-    hist[threadIdx.x] = inc - v;
+  for (int b = 0; b < NRES; ++b) sz[b] = hist[b];
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int r = st.rank[q], b = st.res[q];
+    int pos = 0;
+#pragma unroll
+    for (int g = 0; g < NRES; ++g) pos += min(sz[g], r) + ((g < b && sz[g] > r) ? 1 : 0);
+    st.order[pos] = (unsigned short)q;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < cnt; q += blockDim.x) st.order[hist[st.res[q]] + st.rank[q]] = (unsigned short)q;
   __syncthreads();
 }
 
@@ -197,7 +222,7 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
   using F = Fixed<T>;
   using I = typename F::I;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int hist[32];
+  __shared__ int hist[NRES_SPREAD];
   __shared__ int s_sub;
   __shared__ I s_maxbits;
 
@@ -214,7 +239,7 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
       s_sub = atomicAdd(work, 1);
       s_maxbits = 0;
     }
-    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    if (threadIdx.x < NRES_SPREAD) hist[threadIdx.x] = 0;
     __syncthreads();
     const int sub = s_sub;
     if (sub >= *s.nsub) break;
@@ -225,12 +250,29 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
       tim[t] = 0;
     }
     T mloc = T(0);
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-      Rec r = rec[p0 + q];
-      stage_point<T, D, W>(g, r, q, st, hist);
-      C cv = c[r.idx];
-      sc[q] = cv;
-      mloc = fmax(mloc, fmax(fabs(cv.x), fabs(cv.y)));
+    // records and strengths in batches of four per thread (independent loads in flight)
+    for (int q0 = threadIdx.x; q0 < cnt; q0 += 4 * blockDim.x) {
+      Rec r[4];
+      C cv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < cnt) r[u] = rec[p0 + q];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < cnt) cv[u] = c[r[u].idx];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < cnt) {
+          stage_point<T, D, W, NRES_SPREAD>(g, r[u], q, st, hist);
+          sc[q] = cv[u];
+          mloc = fmax(mloc, fmax(fabs(cv[u].x), fabs(cv[u].y)));
+        }
+      }
     }
     // non-negative floats order like their bit patterns; NaN (all bits high) wins
     if (!(mloc == mloc)) mloc = T(INFINITY);
@@ -239,7 +281,7 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
     else
       atomicMax(reinterpret_cast<unsigned long long*>(&s_maxbits),
                 (unsigned long long)__double_as_longlong((double)mloc));
-    bucket_order<T, D>(cnt, st, hist);
+    bucket_order<T, D, NRES_SPREAD>(cnt, st, hist);
 
     T maxabs;
     if (sizeof(T) == 4)
@@ -255,11 +297,8 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
       inv = T(NAN);  // non-finite strengths: make the whole tile NaN
     }
 
-    const int Q = (cnt + 31) >> 5;
-    for (int sl = threadIdx.x; sl < (Q << 5); sl += blockDim.x) {
-      const int pos = (sl & 31) * Q + (sl >> 5);
-      if (pos >= cnt) continue;
-      const int q = st.order[pos];
+    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+      const int q = st.order[sl];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
       point_weights<T, W>(st.v[q * D], g.B[0], kpar, ts0, k0);
@@ -331,7 +370,7 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
   using C = typename Traits<T>::C;
   using Rec = typename Traits<T>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int hist[32];
+  __shared__ int hist[NRES_INTERP];
   __shared__ int s_sub;
 
   const int ntile = g.ntile, maxsub = g.maxsub;
@@ -342,7 +381,7 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
 
   for (;;) {
     if (threadIdx.x == 0) s_sub = atomicAdd(work, 1);
-    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    if (threadIdx.x < NRES_INTERP) hist[threadIdx.x] = 0;
     __syncthreads();
     const int sub = s_sub;
     if (sub >= *s.nsub) break;
@@ -358,16 +397,28 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
       const long long gy = wrap_idx(org[1] + t1, g.n[1]);
       const long long gz = wrap_idx(org[2] + t2, g.n[2]);
       const C* grow = grid + (gz * g.n[1] + gy) * (long long)g.n[0];
-      for (int t0 = lane; t0 < T0; t0 += 32) tile[row * T0 + t0] = grow[wrap_idx(org[0] + t0, g.n[0])];
+      for (int t0 = lane; t0 < T0; t0 += 32) cp_async_elem(tile + row * T0 + t0, grow + wrap_idx(org[0] + t0, g.n[0]));
     }
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) stage_point<T, D, W>(g, rec[p0 + q], q, st, hist);
-    bucket_order<T, D>(cnt, st, hist);
+    cp_async_commit();
+    // records in batches of four per thread while the tile copies are in flight
+    for (int q0 = threadIdx.x; q0 < cnt; q0 += 4 * blockDim.x) {
+      Rec r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < cnt) r[u] = rec[p0 + q];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < cnt) stage_point<T, D, W, NRES_INTERP>(g, r[u], q, st, hist);
+      }
+    }
+    cp_async_wait_all();
+    bucket_order<T, D, NRES_INTERP>(cnt, st, hist);
 
-    const int Q = (cnt + 31) >> 5;
-    for (int sl = threadIdx.x; sl < (Q << 5); sl += blockDim.x) {
-      const int pos = (sl & 31) * Q + (sl >> 5);
-      if (pos >= cnt) continue;
-      const int q = st.order[pos];
+    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+      const int q = st.order[sl];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
       point_weights<T, W>(st.v[q * D], g.B[0], kpar, ts0, k0);
