@@ -61,6 +61,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest of every rank's value (the slowest rank's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(points_per_rank: int, ms_max: float, world_size: int) -> float:
+    """Whole-job NU points/s: every rank's points over the slowest rank's step time."""
+    return world_size * points_per_rank / (ms_max * 1e-3)
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons while running."""
@@ -188,13 +204,8 @@ def run_cuda(args, ws, rank, local):
     st = (p1.status(), p2.status())
     if st != (0, 0):
         raise RuntimeError("device status %s" % (st,))
-    ms_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * 2 * M / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dev)
+    value = aggregate_value(2 * M, ms_max, ws)
 
     # end to end: pinned host buffers, copies inside the timed region
     e2e = None
@@ -228,10 +239,10 @@ def run_cuda(args, ws, rank, local):
             step_e2e()
         e1.record(stream)
         barrier()
-        ms_e2e = e0.elapsed_time(e1) / ke
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / ke, dev)
         h2d = sum(v.numel() * v.element_size() for v in hx) + hc.numel() * 8 + hf.numel() * 8
         d2h = hfo.numel() * 8 + hco.numel() * 8
-        e2e = {"value": ws * 2 * M / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+        e2e = {"value": aggregate_value(2 * M, ms_e2e, ws), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel
