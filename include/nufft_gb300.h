@@ -176,6 +176,38 @@ int nufft_correction_factors(int64_t N, int64_t n, int w, double beta, double* o
 /* Smallest 2^a 3^b 5^c >= m (m >= 1); returns -1 on overflow or m < 1. */
 int64_t nufft_next235(int64_t m);
 
+/* ------------------------------------------------------------ no allocation
+ * nufft_spread_noalloc -- the spreading step of a complex64 type-1 transform
+ * (fine-grid values b_l of Eq. (bl)) for callers that cannot allocate device
+ * memory: code running under another owner's memory pool or arena, latency-
+ * critical paths that cannot take an allocation's implicit synchronisation,
+ * and plugin hosts that forbid allocation.  The paper has no counterpart; it
+ * is a deployment variant of the plan path above.
+ *
+ * Computes b = spread(x, y, z, c) on the fine grid n[0..dim-1] with kernel
+ * width w and ES parameter beta (take them from nufft_choose_params), and
+ * OVERWRITES grid (n_1 ... n_d complex64, dimension 1 fastest, device
+ * memory) with it.  x, y, z: M float device arrays (y NULL if dim < 2, z NULL
+ * if dim < 3); c: M complex64 device strengths.  Enqueued on stream (a
+ * cudaStream_t, NULL = legacy default); asynchronous.
+ *
+ * It calls no cudaMalloc / cudaFree and no allocating library routine: its
+ * binning arrays live in one static device array of 32 MiB that every GPU
+ * loading the library holds until exit.  All calls share that array and it
+ * keeps the previous call's contents (each call clears what must start at
+ * zero), so calls whose device work overlaps race: serialise them.  The
+ * array's device address is looked up (cudaGetSymbolAddress) during the
+ * first call on each device; make that first call before any stream capture.
+ *
+ * Returns NUFFT_OK; NUFFT_ERR_BAD_ARG (dim, w outside [2, 16], n_i < 2w,
+ * beta <= 0, M < 0, NULL pointer); NUFFT_ERR_TOO_BIG when M points and the
+ * bins of this grid need more than the 32 MiB array (16 bytes per point plus
+ * about 16 bytes per bin: roughly two million points); NUFFT_ERR_CUDA when a
+ * launch fails.
+ */
+int nufft_spread_noalloc(int dim, const int64_t* n, int w, double beta, int64_t M, const float* x,
+                         const float* y, const float* z, const void* c, void* grid, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,8 @@ from . import build as _build
 __all__ = [
     "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
     "nufft_execute", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
-    "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235", "library_path",
+    "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235",
+    "nufft_spread_noalloc", "library_path",
     "NUFFT_C64", "NUFFT_C128",
 ]
 
@@ -76,6 +77,7 @@ def _L():
     lib.nufft_correction_factors.argtypes = [i64, i64, i32, dbl, ctypes.POINTER(ctypes.c_double)]
     lib.nufft_next235.argtypes = [i64]
     lib.nufft_next235.restype = i64
+    lib.nufft_spread_noalloc.argtypes = [i32, pi64, i32, dbl, i64, vp, vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -149,6 +151,16 @@ def nufft_correction_factors(N: int, n: int, w: int, beta: float):
 
 def nufft_next235(m: int) -> int:
     return int(_L().nufft_next235(int(m)))
+
+
+def nufft_spread_noalloc(dim: int, n, w: int, beta: float, M: int, x: int, y: int, z: int, c: int,
+                         grid: int, stream: int | None) -> int:
+    """Spreading onto a caller-provided complex64 fine grid with no device allocation
+    (pointers are device addresses)."""
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in n] + [1] * (3 - len(n))))
+    vp = ctypes.c_void_p
+    return _L().nufft_spread_noalloc(int(dim), arr, int(w), float(beta), int(M), vp(x or 0), vp(y or 0),
+                                     vp(z or 0), vp(c or 0), vp(grid or 0), vp(stream or 0))
 
 
 # --------------------------------------------------------------- torch layer
