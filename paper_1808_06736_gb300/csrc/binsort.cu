@@ -88,28 +88,54 @@ __device__ __forceinline__ T coord(int dim, int j, const T* x, const T* y, const
   return dim == 0 ? x[j] : (dim == 1 ? y[j] : z[j]);
 }
 
+// Fold one point into its bin id; sets *bad for |x| > 3 pi (or non-finite)
+// when chk is on.
+template <typename T>
+__device__ __forceinline__ int point_bin(const Geom& g, const FoldConst& fc, const T* xv, int chk,
+                                         bool* bad) {
+  int bin = 0, stride = 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < g.d) {
+      if (chk) *bad |= !(fabs(xv[i]) <= (T)kThreePi);
+      int cell;
+      T fr;
+      fold(xv[i], g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
+      bin += (cell / g.B[i]) * stride;
+      stride *= g.nb[i];
+    }
+  }
+  return bin;
+}
+
+// Points are handled four per thread per iteration so that twelve independent
+// coordinate loads are in flight before the first one is used.
+constexpr int kILP = 4;
+
 template <typename T>
 __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict__ y,
                              const T* __restrict__ z, Geom g, FoldConst fc, int chk,
                              int* __restrict__ bin_count, int* __restrict__ err) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-    int bin = 0, stride = 1;
-    bool bad = false;
+  const int stride = gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += kILP * stride) {
+    T v[kILP][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (i < g.d) {
-        T xv = coord<T>(i, j, x, y, z);
-        if (chk) bad |= !(fabs(xv) <= (T)kThreePi);
-        int cell;
-        T fr;
-        fold(xv, g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
-        bin += (cell / g.B[i]) * stride;
-        stride *= g.nb[i];
+    for (int u = 0; u < kILP; ++u) {
+      const int j = j0 + u * stride;
+      if (j < M) {
+        v[u][0] = x[j];
+        v[u][1] = g.d > 1 ? y[j] : T(0);
+        v[u][2] = g.d > 2 ? z[j] : T(0);
       }
     }
-    if (chk && bad) atomicCAS(err, 0, NUFFT_ERR_OUT_OF_RANGE);
-    atomicAdd(&bin_count[bin], 1);  // result unused: a fire-and-forget reduction
+#pragma unroll
+    for (int u = 0; u < kILP; ++u) {
+      const int j = j0 + u * stride;
+      if (j < M) atomicAdd(&bin_count[point_bin(g, fc, v[u], chk, &bad)], 1);  // result unused
+    }
   }
+  if (chk && bad) atomicCAS(err, 0, NUFFT_ERR_OUT_OF_RANGE);
 }
 
 // Exclusive scans of the bin counts (-> breakpoints and scatter cursors) and
@@ -186,24 +212,47 @@ template <typename T>
 __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ y,
                           const T* __restrict__ z, Geom g, FoldConst fc, int* __restrict__ cursor,
                           typename Traits<T>::Rec* __restrict__ rec) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-    typename Traits<T>::Rec r;
-    int bin = 0, stride = 1;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += kILP * stride) {
+    T v[kILP][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      r.v[i] = T(0);
-      if (i < g.d) {
-        int cell;
-        T fr;
-        fold(coord<T>(i, j, x, y, z), g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
-        int b = cell / g.B[i];
-        r.v[i] = T(cell - b * g.B[i]) + fr;
-        bin += b * stride;
-        stride *= g.nb[i];
+    for (int u = 0; u < kILP; ++u) {
+      const int j = j0 + u * stride;
+      if (j < M) {
+        v[u][0] = x[j];
+        v[u][1] = g.d > 1 ? y[j] : T(0);
+        v[u][2] = g.d > 2 ? z[j] : T(0);
       }
     }
-    r.idx = j;
-    rec[atomicAdd(&cursor[bin], 1)] = r;  // order inside a bin is arbitrary
+    typename Traits<T>::Rec r[kILP];
+    int dest[kILP];
+#pragma unroll
+    for (int u = 0; u < kILP; ++u) {
+      const int j = j0 + u * stride;
+      if (j < M) {
+        int bin = 0, bstride = 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          r[u].v[i] = T(0);
+          if (i < g.d) {
+            int cell;
+            T fr;
+            fold(v[u][i], g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
+            const int b = cell / g.B[i];
+            r[u].v[i] = T(cell - b * g.B[i]) + fr;
+            bin += b * bstride;
+            bstride *= g.nb[i];
+          }
+        }
+        r[u].idx = j;
+        dest[u] = atomicAdd(&cursor[bin], 1);  // order inside a bin is arbitrary
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kILP; ++u) {
+      const int j = j0 + u * stride;
+      if (j < M) rec[dest[u]] = r[u];
+    }
   }
 }
 

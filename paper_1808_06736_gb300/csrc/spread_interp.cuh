@@ -211,6 +211,57 @@ __device__ __forceinline__ void point_weights(T v, int B, T kpar, int& ts, T* k)
   for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, s, f), kpar);
 }
 
+// Add a fixed-point tile (scaled by inv) into the fine grid with periodic
+// wrapping.  Warps take tile rows; lanes walk along x.  For complex64 rows
+// that do not wrap on a grid with even n_1, neighbouring cells go out as one
+// 16-byte vector reduction (red.global.add.v4.f32) from an even grid index.
+__device__ __forceinline__ void red_add2(float2* p, float a0, float b0, float a1, float b1) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a0), "f"(b0), "f"(a1), "f"(b1)
+               : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void flush_tile(const Geom& g, const int* org, const typename Fixed<T>::I* tre,
+                                           const typename Fixed<T>::I* tim, T inv,
+                                           typename Traits<T>::C* grid) {
+  using C = typename Traits<T>::C;
+  using I = typename Fixed<T>::I;
+  const int T0 = g.T[0];
+  const int nrows = g.ntile / T0;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const bool pairs = (sizeof(T) == 4) && ((g.n[0] & 1) == 0) && org[0] >= 0 && org[0] + T0 <= g.n[0];
+  for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
+    const int t1 = row % g.T[1], t2 = row / g.T[1];
+    const long long gy = wrap_idx(org[1] + t1, g.n[1]);
+    const long long gz = wrap_idx(org[2] + t2, g.n[2]);
+    C* grow = grid + (gz * g.n[1] + gy) * (long long)g.n[0];
+    const I* ar = tre + row * T0;
+    const I* ai = tim + row * T0;
+    if (pairs) {
+      const int first = org[0] & 1;  // a leading single cell when the row starts at an odd index
+      const int nslots = first + (T0 - first + 1) / 2;
+      for (int sl = lane; sl < nslots; sl += 32) {
+        const int t0 = (first && sl == 0) ? 0 : first + 2 * (sl - first);
+        const I a0 = ar[t0], b0 = ai[t0];
+        if (t0 + 1 < T0 && !(first && sl == 0)) {
+          const I a1 = ar[t0 + 1], b1 = ai[t0 + 1];
+          if (a0 != 0 || b0 != 0 || a1 != 0 || b1 != 0)
+            red_add2(reinterpret_cast<float2*>(grow + org[0] + t0), float(a0) * float(inv), float(b0) * float(inv),
+                     float(a1) * float(inv), float(b1) * float(inv));
+        } else if (a0 != 0 || b0 != 0) {
+          red_add(grow + org[0] + t0, T(a0) * inv, T(b0) * inv);
+        }
+      }
+    } else {
+      for (int t0 = lane; t0 < T0; t0 += 32) {
+        const I a = ar[t0], b = ai[t0];
+        if (a == 0 && b == 0) continue;
+        red_add(grow + wrap_idx(org[0] + t0, g.n[0]), T(a) * inv, T(b) * inv);
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------- spread
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
@@ -343,20 +394,7 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
     // tile are spread over the warps, a warp's lanes walk along x
     int org[3];
     tile_origin(g, bin, org);
-    const int nrows = ntile / T0;
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
-      const int t1 = row % g.T[1], t2 = row / g.T[1];
-      const long long gy = wrap_idx(org[1] + t1, g.n[1]);
-      const long long gz = wrap_idx(org[2] + t2, g.n[2]);
-      C* grow = grid + (gz * g.n[1] + gy) * (long long)g.n[0];
-      for (int t0 = lane; t0 < T0; t0 += 32) {
-        const int t = row * T0 + t0;
-        const I a = tre[t], b = tim[t];
-        if (a == 0 && b == 0) continue;
-        red_add(grow + wrap_idx(org[0] + t0, g.n[0]), T(a) * inv, T(b) * inv);
-      }
-    }
+    flush_tile<T>(g, org, tre, tim, inv, grid);
     __syncthreads();
   }
 }

@@ -203,3 +203,20 @@ def test_small_bins_and_subproblems(pkg, oracle_mod):
     b, _ = gpu_transform(pkg, 2, Ns, xs, f, 1e-5, -1, np.complex64, bin_size=(8, 4, 4), max_subprob=64)
     assert oracle_mod.rel_l2(a[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= 1e-4
     assert oracle_mod.rel_l2(b[0], oracle_mod.direct_type2(x64, f, -1, Ns)) <= 1e-4
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-6, 1e-7])
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_spread_widths_3d_c64(pkg, oracle_mod, eps, kind):
+    """3D complex64 spreading for w = 5..8 on uniform and clustered points."""
+    Ns = [36, 30, 20]
+    M = 60000
+    xs, c, _ = case_inputs(3, Ns, M, kind, np.complex64, seed=4000)
+    x64 = [v.astype(np.float64) for v in xs]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    g, info = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, np.complex64)
+    o2 = oracle_mod.type1(x64, c, 1, Ns, w=w, beta=beta, ns=ns)
+    assert oracle_mod.rel_l2(g[0], o2) <= TOL_SAME[np.complex64]
+    # below eps = 1e-5 complex64 is held to its rounding floor (Remark r:rounding), not to 10 eps
+    bar = max(10 * eps, 2e-5)
+    assert oracle_mod.rel_l2(g[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= bar
