@@ -210,40 +210,71 @@ def run_cuda(args, ws, rank, local):
     # end to end: pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
+        # End to end through the public API from pinned host buffers.  Each step
+        # uploads its own points, strengths and coefficients and reads back both
+        # results; uploads run on a copy stream and downloads on another, double
+        # buffered, so step k's copies overlap the compute of its neighbours.
         hx = [v.cpu().pin_memory() for v in xs]
         hc = c.cpu().pin_memory()
         hf = f.cpu().pin_memory()
-        hfo = torch.empty(fout.shape, dtype=torch.complex64).pin_memory()
-        hco = torch.empty(cout.shape, dtype=torch.complex64).pin_memory()
-        dx = [torch.empty_like(v) for v in xs]
-        dc, df = torch.empty_like(c), torch.empty_like(f)
+        nb = 2
+        dx = [[torch.empty_like(v) for v in xs] for _ in range(nb)]
+        dc = [torch.empty_like(c) for _ in range(nb)]
+        df = [torch.empty_like(f) for _ in range(nb)]
+        dfo = [torch.empty_like(fout) for _ in range(nb)]
+        dco = [torch.empty_like(cout) for _ in range(nb)]
+        hfo = [torch.empty(fout.shape, dtype=torch.complex64).pin_memory() for _ in range(nb)]
+        hco = [torch.empty(cout.shape, dtype=torch.complex64).pin_memory() for _ in range(nb)]
+        up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        inputs_free = [torch.cuda.Event() for _ in range(nb)]
+        outputs_free = [torch.cuda.Event() for _ in range(nb)]
+        for ev in inputs_free + outputs_free:
+            ev.record(stream)
 
-        def step_e2e():
-            for a, b in zip(dx, hx):
-                a.copy_(b, non_blocking=True)
-            dc.copy_(hc, non_blocking=True)
-            df.copy_(hf, non_blocking=True)
-            p1.setpts(*dx)
-            p1.execute(dc, out=fout)
-            p2.setpts(*dx)
-            p2.execute(df, out=cout)
-            hfo.copy_(fout, non_blocking=True)
-            hco.copy_(cout, non_blocking=True)
+        def step_e2e(k):
+            b = k % nb
+            ready, done_in, done_out = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+            with torch.cuda.stream(up):
+                up.wait_event(inputs_free[b])
+                for a, h in zip(dx[b], hx):
+                    a.copy_(h, non_blocking=True)
+                dc[b].copy_(hc, non_blocking=True)
+                df[b].copy_(hf, non_blocking=True)
+                ready.record(up)
+            stream.wait_event(ready)
+            stream.wait_event(outputs_free[b])
+            p1.setpts(*dx[b])
+            p1.execute(dc[b], out=dfo[b])
+            p2.setpts(*dx[b])
+            p2.execute(df[b], out=dco[b])
+            done_in.record(stream)
+            inputs_free[b] = done_in
+            with torch.cuda.stream(down):
+                down.wait_event(done_in)
+                hfo[b].copy_(dfo[b], non_blocking=True)
+                hco[b].copy_(dco[b], non_blocking=True)
+                done_out.record(down)
+            outputs_free[b] = done_out
 
-        for _ in range(2):
-            step_e2e()
+        for k in range(2):
+            step_e2e(k)
         barrier()
+        ke = max(4, min(args.steps, 6))
         e0.record(stream)
-        ke = max(3, min(args.steps, 5))
-        for _ in range(ke):
-            step_e2e()
+        up.wait_stream(stream)  # the timed uploads start after e0
+        down.wait_stream(stream)
+        for k in range(ke):
+            step_e2e(k)
+        stream.wait_stream(down)
+        stream.wait_stream(up)
         e1.record(stream)
         barrier()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / ke, dev)
         h2d = sum(v.numel() * v.element_size() for v in hx) + hc.numel() * 8 + hf.numel() * 8
-        d2h = hfo.numel() * 8 + hco.numel() * 8
+        d2h = hfo[0].numel() * 8 + hco[0].numel() * 8
         e2e = {"value": aggregate_value(2 * M, ms_e2e, ws), "unit": UNIT, "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "pipelining": "uploads and downloads on their own streams, double buffered"}
 
     # roofline of the dominant kernel
     med = {k: statistics.median(v) for k, v in slots.items()}

@@ -228,12 +228,12 @@ namespace nufft {
 
 size_t spread_smem_bytes(bool dbl, const Geom& g, int) {
   size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8, ct = dbl ? 8 : 4;
-  return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc +
-         (size_t)g.maxsub * (g.d * ct + 4 + 3 * 2);
+  (void)ct;
+  return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc + (size_t)g.maxsub * 3 * 2;
 }
 size_t interp_smem_bytes(bool dbl, const Geom& g, int) {
-  size_t cc = dbl ? 16 : 8, ct = dbl ? 8 : 4;
-  return (size_t)g.ntile * cc + (size_t)g.maxsub * (g.d * ct + 4 + 3 * 2);
+  size_t cc = dbl ? 16 : 8;
+  return (size_t)g.ntile * cc + (size_t)g.maxsub * 3 * 2;
 }
 
 static cudaError_t si_dispatch(bool spread, bool dbl, const Geom& g, double beta, const Sorted& s,

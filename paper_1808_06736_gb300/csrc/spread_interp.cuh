@@ -122,10 +122,11 @@ constexpr int NRES_INTERP = 16;
 constexpr int NRES_SPREAD = 32;
 
 // Shared-memory layout common to both kernels (after the tile).
+// The points' records stay in global memory (read again, from L2, when a
+// point is processed); shared memory keeps only the ordering state, so that
+// more thread blocks fit on an SM.
 template <typename T, int D>
 struct Stage {
-  T* v;                  // [maxsub * D] coordinates relative to the bin origin
-  int* idx;              // [maxsub] caller index
   unsigned short* res;   // [maxsub] bank group of the stencil corner
   unsigned short* rank;  // [maxsub] rank within its group
   unsigned short* order; // [maxsub] processing order
@@ -133,16 +134,12 @@ struct Stage {
 
 template <typename T, int D>
 __host__ __device__ inline size_t stage_bytes(int maxsub) {
-  return (size_t)maxsub * (D * sizeof(T) + sizeof(int) + 3 * sizeof(unsigned short));
+  return (size_t)maxsub * 3 * sizeof(unsigned short);
 }
 
 template <typename T, int D>
 __device__ __forceinline__ Stage<T, D> carve_stage(unsigned char* p, int maxsub) {
   Stage<T, D> s;
-  s.v = reinterpret_cast<T*>(p);
-  p += (size_t)maxsub * D * sizeof(T);
-  s.idx = reinterpret_cast<int*>(p);
-  p += (size_t)maxsub * sizeof(int);
   s.res = reinterpret_cast<unsigned short*>(p);
   s.rank = s.res + maxsub;
   s.order = s.rank + maxsub;
@@ -169,12 +166,10 @@ __device__ __forceinline__ void stage_point(const Geom& g, const typename Traits
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     T v = r.v[d];
-    st.v[q * D + d] = v;
     int il = min((int)v, g.B[d] - 1);
     base += (il + stencil_step<W>(v - T(il))) * stride;
     stride *= g.T[d];
   }
-  st.idx[q] = r.idx;
   int rr = base & (NRES - 1);
   st.res[q] = (unsigned short)rr;
   st.rank[q] = (unsigned short)atomicAdd(&hist[rr], 1);
@@ -263,8 +258,14 @@ __device__ __forceinline__ void flush_tile(const Geom& g, const int* org, const 
 }
 
 // ----------------------------------------------------------------- spread
+// float kernels are held to 64 registers so four 256-thread blocks fit an SM
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 4 : 2;
+};
+
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T kpar, Sorted s,
                                                 const typename Traits<T>::C* __restrict__ c,
                                                 typename Traits<T>::C* __restrict__ grid,
                                                 int* __restrict__ work) {
@@ -350,16 +351,17 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
 
     for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
       const int q = st.order[sl];
+      const Rec rq = rec[p0 + q];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights<T, W>(st.v[q * D], g.B[0], kpar, ts0, k0);
+      point_weights<T, W>(rq.v[0], g.B[0], kpar, ts0, k0);
       T k1[(D > 1) ? W : 1];
       T f2 = T(0);
       int st2 = 0;
-      if constexpr (D > 1) point_weights<T, W>(st.v[q * D + 1], g.B[1], kpar, ts1, k1);
+      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], kpar, ts1, k1);
       else k1[0] = T(1);
       if constexpr (D > 2) {
-        T v2 = st.v[q * D + 2];
+        T v2 = rq.v[2];
         int il2 = min((int)v2, g.B[2] - 1);
         f2 = v2 - T(il2);
         st2 = stencil_step<W>(f2);
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, T kpar, Sorted s,
 
 // ----------------------------------------------------------------- interp
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T kpar, Sorted s,
                                                 const typename Traits<T>::C* __restrict__ grid,
                                                 typename Traits<T>::C* __restrict__ c,
                                                 int* __restrict__ work) {
@@ -457,16 +459,17 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
 
     for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
       const int q = st.order[sl];
+      const Rec rq = rec[p0 + q];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights<T, W>(st.v[q * D], g.B[0], kpar, ts0, k0);
+      point_weights<T, W>(rq.v[0], g.B[0], kpar, ts0, k0);
       T k1[(D > 1) ? W : 1];
       T f2 = T(0);
       int st2 = 0;
-      if constexpr (D > 1) point_weights<T, W>(st.v[q * D + 1], g.B[1], kpar, ts1, k1);
+      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], kpar, ts1, k1);
       else k1[0] = T(1);
       if constexpr (D > 2) {
-        T v2 = st.v[q * D + 2];
+        T v2 = rq.v[2];
         int il2 = min((int)v2, g.B[2] - 1);
         f2 = v2 - T(il2);
         st2 = stencil_step<W>(f2);
@@ -500,7 +503,7 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, T kpar, Sorted s,
       C out;
       out.x = ar;
       out.y = ai;
-      c[st.idx[q]] = out;
+      c[rq.idx] = out;
     }
     __syncthreads();
   }
