@@ -93,7 +93,7 @@ __device__ __forceinline__ T coord(int dim, int j, const T* x, const T* y, const
 template <typename T>
 __device__ __forceinline__ int point_bin(const Geom& g, const FoldConst& fc, const T* xv, int chk,
                                          bool* bad) {
-  int bin = 0, stride = 1;
+  int b[3] = {0, 0, 0};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i < g.d) {
@@ -101,11 +101,10 @@ __device__ __forceinline__ int point_bin(const Geom& g, const FoldConst& fc, con
       int cell;
       T fr;
       fold(xv[i], g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
-      bin += (cell / g.B[i]) * stride;
-      stride *= g.nb[i];
+      b[i] = cell / g.B[i];
     }
   }
-  return bin;
+  return bin_id(g, b[0], b[1], b[2]);
 }
 
 // Points are handled four per thread per iteration so that twelve independent
@@ -230,7 +229,7 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
     for (int u = 0; u < kILP; ++u) {
       const int j = j0 + u * stride;
       if (j < M) {
-        int bin = 0, bstride = 1;
+        int bb[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           r[u].v[i] = T(0);
@@ -238,14 +237,12 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
             int cell;
             T fr;
             fold(v[u][i], g.n[i], fc.s_hi[i], fc.s_lo[i], fc.s[i], cell, fr);
-            const int b = cell / g.B[i];
-            r[u].v[i] = T(cell - b * g.B[i]) + fr;
-            bin += b * bstride;
-            bstride *= g.nb[i];
+            bb[i] = cell / g.B[i];
+            r[u].v[i] = T(cell - bb[i] * g.B[i]) + fr;
           }
         }
         r[u].idx = j;
-        dest[u] = atomicAdd(&cursor[bin], 1);  // order inside a bin is arbitrary
+        dest[u] = atomicAdd(&cursor[bin_id(g, bb[0], bb[1], bb[2])], 1);  // order inside a bin is arbitrary
       }
     }
 #pragma unroll
@@ -255,6 +252,34 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
     }
   }
 }
+
+}  // namespace
+
+void finish_geom(Geom& g) {
+  // super-blocks of about 64 bins (3D 4x4x4, 2D 8x8, 1D 64)
+  const int sbd[4][3] = {{1, 1, 1}, {64, 1, 1}, {8, 8, 1}, {4, 4, 4}};
+  int nbins = 1, ntile = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (i >= g.d) {
+      g.n[i] = g.n[i] > 0 ? g.n[i] : 1;
+      g.B[i] = 1;
+    }
+    g.T[i] = (i < g.d) ? g.B[i] + g.w : 1;
+    g.nb[i] = (g.n[i] + g.B[i] - 1) / g.B[i];
+    int sb = sbd[g.d][i];
+    while (sb > 1 && sb / 2 >= g.nb[i]) sb /= 2;  // no wider than the grid needs
+    g.sb[i] = sb;
+    g.lsb[i] = 0;
+    while ((1 << g.lsb[i]) < sb) ++g.lsb[i];
+    g.ns[i] = (g.nb[i] + sb - 1) / sb;
+    nbins *= g.ns[i] * sb;
+    ntile *= g.T[i];
+  }
+  g.nbins = nbins;
+  g.ntile = ntile;
+}
+
+namespace {
 
 int grid_for(int64_t work, int threads) {
   int dev = 0, sms = 148;

@@ -61,13 +61,8 @@ void pick_bins(Geom& g) {
   static const int c1[][3] = {{1024, 1, 1}, {512, 1, 1}, {256, 1, 1}, {128, 1, 1}, {64, 1, 1}};
   const int(*c)[3] = g.d == 3 ? c3 : (g.d == 2 ? c2 : c1);
   for (int k = 0; k < 5; ++k) {
-    for (int i = 0; i < 3; ++i) {
-      g.B[i] = i < g.d ? std::max(1, std::min(c[k][i], g.n[i])) : 1;
-      g.T[i] = i < g.d ? g.B[i] + g.w : 1;
-      g.nb[i] = (g.n[i] + g.B[i] - 1) / g.B[i];
-    }
-    g.ntile = g.T[0] * g.T[1] * g.T[2];
-    g.nbins = g.nb[0] * g.nb[1] * g.nb[2];
+    for (int i = 0; i < 3; ++i) g.B[i] = i < g.d ? std::max(1, std::min(c[k][i], g.n[i])) : 1;
+    finish_geom(g);
     if (spread_smem_bytes(false, g, 256) <= 110 * 1024) break;
   }
 }

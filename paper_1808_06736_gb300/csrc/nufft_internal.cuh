@@ -21,10 +21,40 @@ struct Geom {
   int B[3];      // bin extent per dimension
   int nb[3];     // bins per dimension = ceil(n / B)
   int T[3];      // tile extent per dimension = B + w
-  int nbins;     // nb[0] nb[1] nb[2]
+  int sb[3];     // bins per super-block per dimension (powers of two)
+  int lsb[3];    // log2(sb)
+  int ns[3];     // super-blocks per dimension = ceil(nb / sb)
+  int nbins;     // bin ids in use: ns[0] ns[1] ns[2] sb[0] sb[1] sb[2] (ids of padding bins stay empty)
   int ntile;     // T[0] T[1] T[2]
   int maxsub;    // most points in one subproblem
 };
+
+// Bin ids run over super-blocks of sb[0] x sb[1] x sb[2] bins, dimension 1
+// fastest inside a super-block and across super-blocks.  Subproblems are
+// processed in id order, so neighbouring bins -- whose tiles overlap in their
+// halos -- are handled close together in time and their fine-grid lines are
+// still in L2.
+__host__ __device__ __forceinline__ int bin_id(const Geom& g, int b0, int b1, int b2) {
+  const int s0 = b0 >> g.lsb[0], s1 = b1 >> g.lsb[1], s2 = b2 >> g.lsb[2];
+  const int l0 = b0 & (g.sb[0] - 1), l1 = b1 & (g.sb[1] - 1), l2 = b2 & (g.sb[2] - 1);
+  const int sup = (s2 * g.ns[1] + s1) * g.ns[0] + s0;
+  return (((sup << g.lsb[2]) + l2) << (g.lsb[1] + g.lsb[0])) + (l1 << g.lsb[0]) + l0;
+}
+__host__ __device__ __forceinline__ void bin_coords(const Geom& g, int id, int* b) {
+  const int sbv = g.sb[0] * g.sb[1] * g.sb[2];
+  int s = id / sbv, l = id - s * sbv;
+  const int l0 = l % g.sb[0];
+  l /= g.sb[0];
+  const int l1 = l % g.sb[1], l2 = l / g.sb[1];
+  const int s0 = s % g.ns[0];
+  s /= g.ns[0];
+  const int s1 = s % g.ns[1], s2 = s / g.ns[1];
+  b[0] = s0 * g.sb[0] + l0;
+  b[1] = s1 * g.sb[1] + l1;
+  b[2] = s2 * g.sb[2] + l2;
+}
+// Fill T, nb, sb, ns, ntile, nbins from d, w, n and B.
+void finish_geom(Geom& g);
 
 // One binned point: coordinates relative to the origin of its bin, in units
 // of fine-grid cells (v in [0, B)), and its index in the caller's arrays.

@@ -199,12 +199,7 @@ void choose_bins(Geom& g, bool dbl, const nufft_opts& o) {
       if (i >= g.d) b = 1;
       g.B[i] = std::max(1, std::min(b, g.n[i]));
     }
-    for (int i = 0; i < 3; ++i) {
-      g.T[i] = (i < g.d) ? g.B[i] + g.w : 1;
-      g.nb[i] = (g.n[i] + g.B[i] - 1) / g.B[i];
-    }
-    g.ntile = g.T[0] * g.T[1] * g.T[2];
-    g.nbins = g.nb[0] * g.nb[1] * g.nb[2];
+    finish_geom(g);
     size_t need = spread_smem_bytes(dbl, g, 256);
     if (need <= budget || (o.bin_size[0] > 0)) break;
   }
@@ -227,8 +222,7 @@ cudaError_t dev_alloc(P** ptr, size_t bytes) {
 namespace nufft {
 
 size_t spread_smem_bytes(bool dbl, const Geom& g, int) {
-  size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8, ct = dbl ? 8 : 4;
-  (void)ct;
+  size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8;
   return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc + (size_t)g.maxsub * 3 * 2;
 }
 size_t interp_smem_bytes(bool dbl, const Geom& g, int) {

@@ -83,8 +83,40 @@ __device__ __forceinline__ T node_z(int t, int step, T f) {
   return (T(t - W / 2 + step) - f) * (T(2) / T(W));
 }
 
+// L2 eviction-priority policies: fine-grid lines that neighbouring tiles will
+// touch again are kept (evict_last); strengths gathered once per point and
+// results scattered once are let go first (evict_first).
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// gather of one strength, read once
+__device__ __forceinline__ float2 load_once(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.x), "=f"(v.y)
+               : "l"(p), "l"(policy_evict_first()));
+  return v;
+}
+__device__ __forceinline__ double2 load_once(const double2* p) { return *p; }
+// scatter of one result, written once
+__device__ __forceinline__ void store_once(float2* p, float2 v) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y),
+               "l"(policy_evict_first())
+               : "memory");
+}
+__device__ __forceinline__ void store_once(double2* p, double2 v) { *p = v; }
+
 __device__ __forceinline__ void red_add(float2* p, float a, float b) {
-  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+  asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(a), "f"(b),
+               "l"(policy_evict_last())
+               : "memory");
 }
 __device__ __forceinline__ void red_add(double2* p, double a, double b) {
   atomicAdd(&p->x, a);
@@ -148,13 +180,11 @@ __device__ __forceinline__ Stage<T, D> carve_stage(unsigned char* p, int maxsub)
 
 // Decode a bin index into its per-dimension tile origin (bin origin - floor(w/2)).
 __device__ __forceinline__ void tile_origin(const Geom& g, int bin, int* org) {
-  int b0 = bin % g.nb[0];
-  int r = bin / g.nb[0];
-  int b1 = r % g.nb[1];
-  int b2 = r / g.nb[1];
-  org[0] = b0 * g.B[0] - g.half;
-  org[1] = b1 * g.B[1] - g.half;
-  org[2] = b2 * g.B[2] - g.half;
+  int b[3];
+  bin_coords(g, bin, b);
+  org[0] = b[0] * g.B[0] - g.half;
+  org[1] = b[1] * g.B[1] - g.half;
+  org[2] = b[2] * g.B[2] - g.half;
 }
 
 // Store a record in the stage and count it in its bank group.  hist[] must
@@ -211,7 +241,8 @@ __device__ __forceinline__ void point_weights(T v, int B, T kpar, int& ts, T* k)
 // that do not wrap on a grid with even n_1, neighbouring cells go out as one
 // 16-byte vector reduction (red.global.add.v4.f32) from an even grid index.
 __device__ __forceinline__ void red_add2(float2* p, float a0, float b0, float a1, float b1) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a0), "f"(b0), "f"(a1), "f"(b1)
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a0), "f"(b0),
+               "f"(a1), "f"(b1), "l"(policy_evict_last())
                : "memory");
 }
 
@@ -314,7 +345,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T k
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = q0 + u * blockDim.x;
-        if (q < cnt) cv[u] = c[r[u].idx];
+        if (q < cnt) cv[u] = load_once(c + r[u].idx);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -503,7 +534,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T k
       C out;
       out.x = ar;
       out.y = ai;
-      c[rq.idx] = out;
+      store_once(c + rq.idx, out);
     }
     __syncthreads();
   }
