@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=300_000)
+    ap.add_argument("--workload", default="3d", choices=["3d", "batched2d"],
+                    help="3d: the 3D type-1/type-2 workload (default); batched2d: many uneven 2D type-2 "
+                         "transforms, batched plan against one plan per transform")
+    ap.add_argument("--B", type=int, default=1024, help="transforms in the batched2d workload")
     return ap.parse_args()
 
 
@@ -358,6 +362,85 @@ def run_reference(args):
     return 0
 
 
+def run_batched2d(args):
+    """1024 independent 2D type-2 transforms, complex64, eps = 1e-5: N per transform uniform in
+    {64^2, 128^2, 256^2, 512^2}, M log-uniform in [1e3, 1e6] uniform points, coefficients re/im
+    N(0, 1).  Batched: one BatchPlan (one launch per step, CUDA graph).  Plain: one Plan per
+    transform, setpts + execute per call.  Both time setpts + execute of every transform."""
+    import numpy as np
+    import torch
+
+    import nufft_inputs as I
+    import paper_1808_06736_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = I.rng(7000)
+    B = args.B
+    sizes = [64, 128, 256, 512]
+    modes = [(int(v), int(v)) for v in rng.choice(sizes, size=B)]
+    Ms = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=B)).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum(Ms)]).astype(np.int64)
+    Mtot = int(offs[-1])
+    xs = I.torch_points(7001, Mtot, 2, "uniform", dev, torch.float32)
+    nf = sum(m[0] * m[1] for m in modes)
+    f = I.torch_complex_normal(7002, nf, dev, torch.complex64)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    bp = pkg.BatchPlan(2, modes, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev)
+    cout = torch.empty(Mtot, dtype=torch.complex64, device=dev)
+
+    def step_batched():
+        bp.setpts(*xs, offsets=offs)
+        bp.execute(f, out=cout)
+
+    for _ in range(args.warmup):
+        step_batched()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_batched()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / args.steps
+    assert bp.status() == 0
+
+    plans = [pkg.Plan(2, m, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev) for m in modes]
+    moffs = bp.mode_offsets
+    couts = [cout[int(offs[t]):int(offs[t + 1])] for t in range(B)]
+    fs = [f[moffs[t]:moffs[t + 1]] for t in range(B)]
+    xts = [[v[int(offs[t]):int(offs[t + 1])] for v in xs] for t in range(B)]
+
+    def step_plain():
+        for t in range(B):
+            plans[t].setpts(*xts[t])
+            plans[t].execute(fs[t], out=couts[t].view(1, -1))
+
+    step_plain()
+    torch.cuda.synchronize()
+    kp = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(kp):
+        step_plain()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1) / kp
+    for p in plans:
+        p.close()
+    bp.close()
+    line = {"metric": "batched 2D type-2 NU points/s (%d transforms, eps=%g, fp32)" % (B, args.eps),
+            "value": Mtot / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched2d", "transforms": B, "modes": "uniform in {64,128,256,512}^2",
+                       "M": "log-uniform in [1e3, 1e6]", "points_total": Mtot, "step": "setpts + execute of all"},
+            "plain": {"value": Mtot / (ms_p * 1e-3), "ms_per_step": ms_p, "path": "one Plan per transform"},
+            "speedup_vs_plain": ms_p / ms_b}
+    print(json.dumps(line))
+    return 0
+
+
 def config_dict(args):
     return {"workload": "3D type 1 + type 2, N=%d^3 modes (fine grid %d^3), M=%d %s points, complex64, eps=%g"
                         % (args.N, 2 * args.N, args.M, args.kind, args.eps),
@@ -372,6 +455,8 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched2d":
+        return run_batched2d(args)
     r = run_cuda(args, ws, rank, local)
     if rank != 0:
         return 0

@@ -19,7 +19,8 @@ __all__ = [
     "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
     "nufft_execute", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
     "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235",
-    "nufft_spread_noalloc", "library_path",
+    "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
+    "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy",
     "NUFFT_C64", "NUFFT_C128",
 ]
 
@@ -78,6 +79,12 @@ def _L():
     lib.nufft_next235.argtypes = [i64]
     lib.nufft_next235.restype = i64
     lib.nufft_spread_noalloc.argtypes = [i32, pi64, i32, dbl, i64, vp, vp, vp, vp, vp, vp]
+    lib.nufft_batch_makeplan.argtypes = [i32, i32, i32, pi64, i32, dbl, i32, vp, ctypes.POINTER(nufft_opts),
+                                         ctypes.POINTER(vp)]
+    lib.nufft_batch_setpts.argtypes = [vp, pi64, vp, vp, vp]
+    lib.nufft_batch_execute.argtypes = [vp, vp, vp]
+    lib.nufft_batch_get_status.argtypes = [vp]
+    lib.nufft_batch_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -161,6 +168,36 @@ def nufft_spread_noalloc(dim: int, n, w: int, beta: float, M: int, x: int, y: in
     vp = ctypes.c_void_p
     return _L().nufft_spread_noalloc(int(dim), arr, int(w), float(beta), int(M), vp(x or 0), vp(y or 0),
                                      vp(z or 0), vp(c or 0), vp(grid or 0), vp(stream or 0))
+
+
+def nufft_batch_makeplan(type_: int, dim: int, nmodes, isign: int, eps: float, prec: int, stream: int | None,
+                         opts: nufft_opts | None):
+    """nmodes: list of B mode-count tuples.  Returns (status, handle)."""
+    B = len(nmodes)
+    flat = [int(v) for m in nmodes for v in m]
+    arr = (ctypes.c_int64 * len(flat))(*flat)
+    h = ctypes.c_void_p()
+    st = _L().nufft_batch_makeplan(int(type_), int(dim), B, arr, int(isign), float(eps), int(prec),
+                                   ctypes.c_void_p(stream or 0), ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(h))
+    return st, h
+
+
+def nufft_batch_setpts(plan, offsets, x: int, y: int, z: int) -> int:
+    arr = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+    return _L().nufft_batch_setpts(plan, arr, ctypes.c_void_p(x or 0), ctypes.c_void_p(y or 0), ctypes.c_void_p(z or 0))
+
+
+def nufft_batch_execute(plan, c: int, f: int) -> int:
+    return _L().nufft_batch_execute(plan, ctypes.c_void_p(c or 0), ctypes.c_void_p(f or 0))
+
+
+def nufft_batch_get_status(plan) -> int:
+    return _L().nufft_batch_get_status(plan)
+
+
+def nufft_batch_destroy(plan) -> int:
+    return _L().nufft_batch_destroy(plan)
 
 
 # --------------------------------------------------------------- torch layer
@@ -280,6 +317,111 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             nufft_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """B independent transforms of one type / dimension / precision / eps with their own
+    mode counts, run as one launch per step (replayed from a CUDA graph).
+
+    ``setpts(x, y, z, offsets)``: concatenated coordinates, transform t owning
+    points offsets[t]..offsets[t+1]-1.  type 1: ``execute(c)`` returns all mode
+    arrays concatenated (``mode_offsets`` gives each start); type 2:
+    ``execute(f)`` with the concatenated mode arrays returns the concatenated
+    values at the points.
+    """
+
+    def __init__(self, nufft_type: int, modes, eps: float = 1e-6, isign: int | None = None, dtype=None,
+                 device=None, stream=None, **opts):
+        import torch
+        self._torch = torch
+        self.type = int(nufft_type)
+        self.modes = [tuple(int(v) for v in m) for m in modes]
+        self.B = len(self.modes)
+        self.dim = len(self.modes[0])
+        if any(len(m) != self.dim for m in self.modes):
+            raise ValueError("all transforms need the same dimension")
+        self.isign = int(isign) if isign is not None else (1 if self.type == 1 else -1)
+        self.dtype = dtype if dtype is not None else torch.complex64
+        self.real_dtype = torch.float32 if self.dtype == torch.complex64 else torch.float64
+        prec = NUFFT_C64 if self.dtype == torch.complex64 else NUFFT_C128
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.mode_offsets = [0]
+        for m in self.modes:
+            n = 1
+            for v in m:
+                n *= v
+            self.mode_offsets.append(self.mode_offsets[-1] + n)
+        self._h = None
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            o = nufft_default_opts()
+            for k, v in opts.items():
+                if k == "bin_size":
+                    for i, b in enumerate(v):
+                        o.bin_size[i] = int(b)
+                else:
+                    setattr(o, k, int(v))
+            st, h = nufft_batch_makeplan(self.type, self.dim, self.modes, self.isign, eps, prec,
+                                         self.stream.cuda_stream, o)
+            if st < 0:
+                raise NufftError(st, "nufft_batch_makeplan")
+            self._h = h
+        self.M = None
+
+    def setpts(self, x, y=None, z=None, offsets=None):
+        torch = self._torch
+        coords = [x, y, z][: self.dim]
+        dev = [torch.as_tensor(v).to(device=self.device, dtype=self.real_dtype, non_blocking=True).contiguous()
+               for v in coords]
+        M = dev[0].numel()
+        if offsets is None or len(offsets) != self.B + 1 or int(offsets[-1]) != M:
+            raise ValueError("offsets must have B + 1 entries ending at the number of points")
+        ptrs = [v.data_ptr() for v in dev] + [0] * (3 - self.dim)
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft_batch_setpts(self._h, [int(v) for v in offsets], *ptrs)
+        if st < 0:
+            raise NufftError(st, "nufft_batch_setpts")
+        self.M = M
+        self._keep = tuple(dev)
+        return self
+
+    def execute(self, data, out=None):
+        torch = self._torch
+        if self.M is None:
+            raise NufftError(-6, "BatchPlan.execute")
+        d = torch.as_tensor(data).to(device=self.device, dtype=self.dtype, non_blocking=True).contiguous()
+        if self.type == 1:
+            if d.numel() != self.M:
+                raise ValueError("expected %d strengths" % self.M)
+            res = out if out is not None else torch.empty(self.mode_offsets[-1], dtype=self.dtype, device=self.device)
+            c_ptr, f_ptr = d.data_ptr(), res.data_ptr()
+        else:
+            if d.numel() != self.mode_offsets[-1]:
+                raise ValueError("expected %d coefficients" % self.mode_offsets[-1])
+            res = out if out is not None else torch.empty(self.M, dtype=self.dtype, device=self.device)
+            c_ptr, f_ptr = res.data_ptr(), d.data_ptr()
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft_batch_execute(self._h, c_ptr, f_ptr)
+        if st < 0:
+            raise NufftError(st, "nufft_batch_execute")
+        self._keep_exec = (d, res)
+        return res
+
+    def status(self) -> int:
+        return nufft_batch_get_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            nufft_batch_destroy(self._h)
         self._h = None
 
     def __del__(self):

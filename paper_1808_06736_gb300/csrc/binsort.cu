@@ -111,10 +111,34 @@ __device__ __forceinline__ int point_bin(const Geom& g, const FoldConst& fc, con
 // coordinate loads are in flight before the first one is used.
 constexpr int kILP = 4;
 
+// For a batch of transforms, the point's transform (found from the point
+// offsets) supplies the fine grid and bin layout, and its bins start at the
+// transform's first global bin id.
+template <typename T>
+__device__ __forceinline__ int point_bin_batch(const Geom& g0, const BatchTable& bt, int j, const T* xv, int chk,
+                                               bool* bad) {
+  const int t = batch_find(bt.poff, bt.B, j);
+  const BatchGeom& tg = bt.bg[t];
+  Geom g = g0;
+  batch_apply(g, tg);
+  int b[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i < g.d) {
+      if (chk) *bad |= !(fabs(xv[i]) <= (T)kThreePi);
+      int cell;
+      T fr;
+      fold(xv[i], g.n[i], tg.fs_hi[i], tg.fs_lo[i], tg.fs[i], cell, fr);
+      b[i] = cell / g.B[i];
+    }
+  }
+  return tg.boff + bin_id(g, b[0], b[1], b[2]);
+}
+
 template <typename T>
 __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict__ y,
                              const T* __restrict__ z, Geom g, FoldConst fc, int chk,
-                             int* __restrict__ bin_count, int* __restrict__ err) {
+                             int* __restrict__ bin_count, int* __restrict__ err, BatchTable bt) {
   const int stride = gridDim.x * blockDim.x;
   bool bad = false;
   for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += kILP * stride) {
@@ -131,7 +155,10 @@ __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict
 #pragma unroll
     for (int u = 0; u < kILP; ++u) {
       const int j = j0 + u * stride;
-      if (j < M) atomicAdd(&bin_count[point_bin(g, fc, v[u], chk, &bad)], 1);  // result unused
+      if (j < M) {
+        const int bin = bt.B > 0 ? point_bin_batch(g, bt, j, v[u], chk, &bad) : point_bin(g, fc, v[u], chk, &bad);
+        atomicAdd(&bin_count[bin], 1);  // result unused
+      }
     }
   }
   if (chk && bad) atomicCAS(err, 0, NUFFT_ERR_OUT_OF_RANGE);
@@ -209,8 +236,8 @@ __global__ void k_sublist(int nbins, int maxsub, const int* __restrict__ cnt,
 
 template <typename T>
 __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ y,
-                          const T* __restrict__ z, Geom g, FoldConst fc, int* __restrict__ cursor,
-                          typename Traits<T>::Rec* __restrict__ rec) {
+                          const T* __restrict__ z, Geom g0, FoldConst fc0, int* __restrict__ cursor,
+                          typename Traits<T>::Rec* __restrict__ rec, BatchTable bt) {
   const int stride = gridDim.x * blockDim.x;
   for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += kILP * stride) {
     T v[kILP][3];
@@ -219,8 +246,8 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
       const int j = j0 + u * stride;
       if (j < M) {
         v[u][0] = x[j];
-        v[u][1] = g.d > 1 ? y[j] : T(0);
-        v[u][2] = g.d > 2 ? z[j] : T(0);
+        v[u][1] = g0.d > 1 ? y[j] : T(0);
+        v[u][2] = g0.d > 2 ? z[j] : T(0);
       }
     }
     typename Traits<T>::Rec r[kILP];
@@ -229,6 +256,19 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
     for (int u = 0; u < kILP; ++u) {
       const int j = j0 + u * stride;
       if (j < M) {
+        Geom g = g0;
+        FoldConst fc = fc0;
+        int boff = 0;
+        if (bt.B > 0) {
+          const BatchGeom& tg = bt.bg[batch_find(bt.poff, bt.B, j)];
+          batch_apply(g, tg);
+          boff = tg.boff;
+          for (int i = 0; i < 3; ++i) {
+            fc.s[i] = tg.fs[i];
+            fc.s_hi[i] = tg.fs_hi[i];
+            fc.s_lo[i] = tg.fs_lo[i];
+          }
+        }
         int bb[3] = {0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -242,7 +282,7 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
           }
         }
         r[u].idx = j;
-        dest[u] = atomicAdd(&cursor[bin_id(g, bb[0], bb[1], bb[2])], 1);  // order inside a bin is arbitrary
+        dest[u] = atomicAdd(&cursor[boff + bin_id(g, bb[0], bb[1], bb[2])], 1);  // order inside a bin is arbitrary
       }
     }
 #pragma unroll
@@ -296,27 +336,27 @@ template <typename T>
 cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, const void* y,
                      const void* z, int chk, int* bin_count, int* bin_start, int* sub_first,
                      int* cursor, void* rec, int* sub_bin, int* sub_pt0, int* sub_cnt, int* nsub,
-                     int* err, cudaStream_t st, cudaEvent_t* ev) {
+                     int* err, cudaStream_t st, cudaEvent_t* ev, const BatchTable& bt, int nbins) {
   const T* xp = (const T*)x;
   const T* yp = g.d > 1 ? (const T*)y : xp;
   const T* zp = g.d > 2 ? (const T*)z : xp;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], st);
-  if ((e = cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)g.nbins, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)nbins, st)) != cudaSuccess) return e;
   if (M > 0) {
-    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, bin_count, err);
+    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, bin_count, err, bt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
-  k_scan<<<1, 1024, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start, cursor, sub_first, nsub);
+  k_scan<<<1, 1024, 0, st>>>(nbins, g.maxsub, bin_count, bin_start, cursor, sub_first, nsub);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sublist<<<grid_for(g.nbins, 256), 256, 0, st>>>(g.nbins, g.maxsub, bin_count, bin_start,
-                                                     sub_first, sub_bin, sub_pt0, sub_cnt);
+  k_sublist<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, g.maxsub, bin_count, bin_start,
+                                                   sub_first, sub_bin, sub_pt0, sub_cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], st);
   if (M > 0) {
     k_scatter<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, cursor,
-                                                    (typename Traits<T>::Rec*)rec);
+                                                    (typename Traits<T>::Rec*)rec, bt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[3], st);
@@ -329,12 +369,13 @@ cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t 
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
                           int* sub_first, int* cursor, void* rec, int* sub_bin,
                           int* sub_pt0, int* sub_cnt, int* nsub, int* err, cudaStream_t st,
-                          cudaEvent_t* ev) {
+                          cudaEvent_t* ev, const BatchTable& bt, int nbins) {
+  if (nbins <= 0) nbins = g.nbins;
   if (dbl)
     return setpts_t<double>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
-                            rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev);
+                            rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev, bt, nbins);
   return setpts_t<float>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
-                         rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev);
+                         rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev, bt, nbins);
 }
 
 }  // namespace nufft

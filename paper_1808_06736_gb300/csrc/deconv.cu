@@ -24,14 +24,13 @@ __device__ __forceinline__ int k_to_pos(int k, int N, int modeord) {
   return k >= 0 ? k : k + N;
 }
 
+// One row (fixed k_2, k_3) of the deconvolution: threads walk k_1.
 template <typename T>
-__global__ void k_deconv(ModeGeom m, const typename Traits<T>::C* __restrict__ grid,
-                         typename Traits<T>::C* __restrict__ f, const T* __restrict__ p1,
-                         const T* __restrict__ p2, const T* __restrict__ p3) {
+__device__ __forceinline__ void deconv_row(const ModeGeom& m, int m2, int m3,
+                                           const typename Traits<T>::C* __restrict__ grid,
+                                           typename Traits<T>::C* __restrict__ f, const T* __restrict__ p1,
+                                           const T* __restrict__ p2, const T* __restrict__ p3) {
   using C = typename Traits<T>::C;
-  const int nrows = m.N[1] * m.N[2];
-  for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
-  const int m2 = row % m.N[1], m3 = row / m.N[1];
   const int k2 = pos_to_k(m2, m.N[1], m.modeord), k3 = pos_to_k(m3, m.N[2], m.modeord);
   const int l2 = k2 < 0 ? k2 + m.n[1] : k2, l3 = k3 < 0 ? k3 + m.n[2] : k3;
   const T p23 = p2[k2 + m.N[1] / 2] * p3[k3 + m.N[2] / 2];
@@ -47,17 +46,15 @@ __global__ void k_deconv(ModeGeom m, const typename Traits<T>::C* __restrict__ g
     o.y = b.y * p;
     frow[m1] = o;
   }
-  }
 }
 
+// One fine-grid row (fixed l_2, l_3) of the pre-correction: threads walk l_1.
 template <typename T>
-__global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict__ f,
-                             typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
-                             const T* __restrict__ p2, const T* __restrict__ p3) {
+__device__ __forceinline__ void precorrect_row(const ModeGeom& m, int l2, int l3,
+                                               const typename Traits<T>::C* __restrict__ f,
+                                               typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
+                                               const T* __restrict__ p2, const T* __restrict__ p3) {
   using C = typename Traits<T>::C;
-  const int nrows = m.n[1] * m.n[2];
-  for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
-  const int l2 = row % m.n[1], l3 = row / m.n[1];
   // fine-grid index l <-> mode k = l (l < N - N/2) or l - n (l >= n - N/2)
   const int k2 = l2 < m.N[1] - m.N[1] / 2 ? l2 : l2 - m.n[1];
   const int k3 = l3 < m.N[2] - m.N[2] / 2 ? l3 : l3 - m.n[2];
@@ -66,7 +63,7 @@ __global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict
   const C zero = {T(0), T(0)};
   if (!in23) {
     for (int l1 = blockIdx.x * blockDim.x + threadIdx.x; l1 < m.n[0]; l1 += gridDim.x * blockDim.x) grow[l1] = zero;
-    continue;
+    return;
   }
   const T p23 = p2[k2 + m.N[1] / 2] * p3[k3 + m.N[2] / 2];
   const C* frow = f + ((long long)k_to_pos(k3, m.N[2], m.modeord) * m.N[1] + k_to_pos(k2, m.N[1], m.modeord)) *
@@ -82,6 +79,61 @@ __global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict
     }
     grow[l1] = o;
   }
+}
+
+template <typename T>
+__global__ void k_deconv(ModeGeom m, const typename Traits<T>::C* __restrict__ grid,
+                         typename Traits<T>::C* __restrict__ f, const T* __restrict__ p1,
+                         const T* __restrict__ p2, const T* __restrict__ p3) {
+  const int nrows = m.N[1] * m.N[2];
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) deconv_row<T>(m, row % m.N[1], row / m.N[1], grid, f, p1, p2, p3);
+}
+
+template <typename T>
+__global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict__ f,
+                             typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
+                             const T* __restrict__ p2, const T* __restrict__ p3) {
+  const int nrows = m.n[1] * m.n[2];
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) precorrect_row<T>(m, row % m.n[1], row / m.n[1], f, grid, p1, p2, p3);
+}
+
+// Batched: rows of all transforms in one launch; a row's transform comes from
+// the per-transform first-row table.
+__device__ __forceinline__ ModeGeom batch_modegeom(const BatchGeom& tg, int d, int modeord) {
+  ModeGeom m;
+  m.d = d;
+  m.modeord = modeord;
+  for (int i = 0; i < 3; ++i) {
+    m.N[i] = tg.N[i];
+    m.n[i] = tg.n[i];
+  }
+  return m;
+}
+
+template <typename T>
+__global__ void k_deconv_batch(int d, int modeord, long long nrows, BatchTable bt, const typename Traits<T>::C* __restrict__ grid,
+                               typename Traits<T>::C* __restrict__ f, const T* __restrict__ pk) {
+  for (long long row = blockIdx.y; row < nrows; row += gridDim.y) {
+    const int t = batch_find(bt.mrowoff, bt.B, row);
+    const BatchGeom& tg = bt.bg[t];
+    const ModeGeom m = batch_modegeom(tg, d, modeord);
+    const int r = (int)(row - tg.mrowoff);
+    deconv_row<T>(m, r % m.N[1], r / m.N[1], grid + tg.goff, f + tg.moff, pk + tg.pkoff[0], pk + tg.pkoff[1],
+                  pk + tg.pkoff[2]);
+  }
+}
+
+template <typename T>
+__global__ void k_precorrect_batch(int d, int modeord, long long nrows, BatchTable bt,
+                                   const typename Traits<T>::C* __restrict__ f, typename Traits<T>::C* __restrict__ grid,
+                                   const T* __restrict__ pk) {
+  for (long long row = blockIdx.y; row < nrows; row += gridDim.y) {
+    const int t = batch_find(bt.growoff, bt.B, row);
+    const BatchGeom& tg = bt.bg[t];
+    const ModeGeom m = batch_modegeom(tg, d, modeord);
+    const int r = (int)(row - tg.growoff);
+    precorrect_row<T>(m, r % m.n[1], r / m.n[1], f + tg.moff, grid + tg.goff, pk + tg.pkoff[0], pk + tg.pkoff[1],
+                      pk + tg.pkoff[2]);
   }
 }
 
@@ -114,7 +166,43 @@ cudaError_t precorrect_t(const ModeGeom& m, const void* f, void* grid, const voi
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t deconv_batch_t(int d, int modeord, long long nrows, int maxlen, const BatchTable& bt, const void* grid,
+                           void* f, const void* pk, cudaStream_t st) {
+  int bx = (maxlen + 255) / 256;
+  long long by = (152LL * 8 + bx - 1) / bx;
+  if (by > nrows) by = nrows;
+  if (by > 65535) by = 65535;
+  if (by < 1) by = 1;
+  k_deconv_batch<T><<<dim3(bx, (unsigned)by, 1), 256, 0, st>>>(d, modeord, nrows, bt, (const typename Traits<T>::C*)grid,
+                                                               (typename Traits<T>::C*)f, (const T*)pk);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t precorrect_batch_t(int d, int modeord, long long nrows, int maxlen, const BatchTable& bt, const void* f,
+                               void* grid, const void* pk, cudaStream_t st) {
+  int bx = (maxlen + 255) / 256;
+  long long by = (152LL * 8 + bx - 1) / bx;
+  if (by > nrows) by = nrows;
+  if (by > 65535) by = 65535;
+  if (by < 1) by = 1;
+  k_precorrect_batch<T><<<dim3(bx, (unsigned)by, 1), 256, 0, st>>>(d, modeord, nrows, bt, (const typename Traits<T>::C*)f,
+                                                                   (typename Traits<T>::C*)grid, (const T*)pk);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_deconv_batch(bool dbl, int d, int modeord, long long nrows, int maxlen, const BatchTable& bt,
+                                const void* grid, void* f, const void* pk, cudaStream_t st) {
+  return dbl ? deconv_batch_t<double>(d, modeord, nrows, maxlen, bt, grid, f, pk, st)
+             : deconv_batch_t<float>(d, modeord, nrows, maxlen, bt, grid, f, pk, st);
+}
+cudaError_t launch_precorrect_batch(bool dbl, int d, int modeord, long long nrows, int maxlen, const BatchTable& bt,
+                                    const void* f, void* grid, const void* pk, cudaStream_t st) {
+  return dbl ? precorrect_batch_t<double>(d, modeord, nrows, maxlen, bt, f, grid, pk, st)
+             : precorrect_batch_t<float>(d, modeord, nrows, maxlen, bt, f, grid, pk, st);
+}
 
 cudaError_t launch_deconv(bool dbl, const ModeGeom& m, const void* grid, void* f, const void* p1,
                           const void* p2, const void* p3, cudaStream_t st) {

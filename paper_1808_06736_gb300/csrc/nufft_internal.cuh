@@ -81,6 +81,53 @@ struct Traits<double> {
   using Rec = RecD;
 };
 
+// Per-transform geometry of a batch of transforms that share d, w, the bin
+// extents B (so tiles have one size) and precision, but not their mode counts.
+struct BatchGeom {
+  int n[3], nb[3], ns[3], sb[3], lsb[3];
+  int N[3];
+  int nbins;          // bin ids of this transform
+  int boff;           // its first global bin id
+  long long goff;     // its fine grid within the batch grid (complex elements)
+  long long moff;     // its modes within the batch mode array (complex elements)
+  int pkoff[3];       // its correction factors within the batch factor array
+  long long growoff;  // its first fine-grid row (n_2 n_3 rows) among all transforms
+  long long mrowoff;  // its first mode row (N_2 N_3 rows) among all transforms
+  double fs[3];       // n / (2 pi) per dimension, and its float hi / lo split
+  float fs_hi[3], fs_lo[3];
+};
+// Passed to the kernels; B = 0 means a single transform (no table).
+struct BatchTable {
+  const BatchGeom* bg;  // [B]
+  const int* boff;      // [B + 1] first global bin id of each transform
+  const int* poff;      // [B + 1] first point of each transform
+  const long long* growoff;  // [B + 1]
+  const long long* mrowoff;  // [B + 1]
+  int B;
+};
+
+// index t with first[t] <= key < first[t + 1] (first ascending, first[0] = 0)
+template <typename I>
+__host__ __device__ __forceinline__ int batch_find(const I* first, int B, I key) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= key) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__host__ __device__ __forceinline__ void batch_apply(Geom& g, const BatchGeom& t) {
+  for (int i = 0; i < 3; ++i) {
+    g.n[i] = t.n[i];
+    g.nb[i] = t.nb[i];
+    g.ns[i] = t.ns[i];
+    g.sb[i] = t.sb[i];
+    g.lsb[i] = t.lsb[i];
+  }
+  g.nbins = t.nbins;
+}
+
 // Device arrays produced by setpts and read by spread / interp.
 struct Sorted {
   const void* rec;     // RecF / RecD [M], in bin order
@@ -103,7 +150,9 @@ cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t 
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
                           int* sub_first, int* cursor, void* rec, int* sub_bin, int* sub_pt0,
                           int* sub_cnt, int* nsub, int* err, cudaStream_t st,
-                          cudaEvent_t* ev /* 4 events or nullptr */);
+                          cudaEvent_t* ev /* 4 events or nullptr */,
+                          const BatchTable& bt = BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0},
+                          int nbins = 0 /* bin ids over all transforms; 0: g.nbins */);
 
 // --- spread / interp (spread_interp_*.cu) --------------------------------------
 struct LaunchCfg {
@@ -119,16 +168,20 @@ cudaError_t spread_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg);
 cudaError_t interp_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg);
 
 cudaError_t launch_spread(bool dbl, const Geom& g, double beta, const Sorted& s, const void* c,
-                          void* grid, int* work, const LaunchCfg& cfg, cudaStream_t st);
+                          void* grid, int* work, const LaunchCfg& cfg, cudaStream_t st,
+                          const BatchTable& bt = BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0});
 cudaError_t launch_interp(bool dbl, const Geom& g, double beta, const Sorted& s, const void* grid,
-                          void* c, int* work, const LaunchCfg& cfg, cudaStream_t st);
+                          void* c, int* work, const LaunchCfg& cfg, cudaStream_t st,
+                          const BatchTable& bt = BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0});
 
 // per-precision, per-dimension entry points (one translation unit each)
 #define NUFFT_DECL_SI(P, D)                                                                      \
   cudaError_t spread_##P##_d##D(const Geom&, double, const Sorted&, const void*, void*, int*,   \
-                                const LaunchCfg&, cudaStream_t, bool configure_only);           \
+                                const LaunchCfg&, cudaStream_t, bool configure_only,            \
+                                const BatchTable&);                                             \
   cudaError_t interp_##P##_d##D(const Geom&, double, const Sorted&, const void*, void*, int*,   \
-                                const LaunchCfg&, cudaStream_t, bool configure_only);
+                                const LaunchCfg&, cudaStream_t, bool configure_only,            \
+                                const BatchTable&);
 NUFFT_DECL_SI(f32, 1)
 NUFFT_DECL_SI(f32, 2)
 NUFFT_DECL_SI(f32, 3)
@@ -148,5 +201,11 @@ cudaError_t launch_deconv(bool dbl, const ModeGeom& m, const void* grid, void* f
                           const void* p2, const void* p3, cudaStream_t st);
 cudaError_t launch_precorrect(bool dbl, const ModeGeom& m, const void* f, void* grid, const void* p1,
                               const void* p2, const void* p3, cudaStream_t st);
+// all transforms of a batch in one launch: nrows rows in total, maxlen the
+// longest row; pk holds every transform's correction factors
+cudaError_t launch_deconv_batch(bool dbl, int d, int modeord, long long nrows, int maxlen, const BatchTable& bt,
+                                const void* grid, void* f, const void* pk, cudaStream_t st);
+cudaError_t launch_precorrect_batch(bool dbl, int d, int modeord, long long nrows, int maxlen, const BatchTable& bt,
+                                    const void* f, void* grid, const void* pk, cudaStream_t st);
 
 }  // namespace nufft

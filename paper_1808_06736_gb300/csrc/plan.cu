@@ -232,25 +232,25 @@ size_t interp_smem_bytes(bool dbl, const Geom& g, int) {
 
 static cudaError_t si_dispatch(bool spread, bool dbl, const Geom& g, double beta, const Sorted& s,
                                const void* a, void* b, int* work, const LaunchCfg& cfg,
-                               cudaStream_t st, bool conf) {
+                               cudaStream_t st, bool conf, const BatchTable& bt) {
   if (spread) {
     if (!dbl) {
-      if (g.d == 1) return spread_f32_d1(g, beta, s, a, b, work, cfg, st, conf);
-      if (g.d == 2) return spread_f32_d2(g, beta, s, a, b, work, cfg, st, conf);
-      return spread_f32_d3(g, beta, s, a, b, work, cfg, st, conf);
+      if (g.d == 1) return spread_f32_d1(g, beta, s, a, b, work, cfg, st, conf, bt);
+      if (g.d == 2) return spread_f32_d2(g, beta, s, a, b, work, cfg, st, conf, bt);
+      return spread_f32_d3(g, beta, s, a, b, work, cfg, st, conf, bt);
     }
-    if (g.d == 1) return spread_f64_d1(g, beta, s, a, b, work, cfg, st, conf);
-    if (g.d == 2) return spread_f64_d2(g, beta, s, a, b, work, cfg, st, conf);
-    return spread_f64_d3(g, beta, s, a, b, work, cfg, st, conf);
+    if (g.d == 1) return spread_f64_d1(g, beta, s, a, b, work, cfg, st, conf, bt);
+    if (g.d == 2) return spread_f64_d2(g, beta, s, a, b, work, cfg, st, conf, bt);
+    return spread_f64_d3(g, beta, s, a, b, work, cfg, st, conf, bt);
   }
   if (!dbl) {
-    if (g.d == 1) return interp_f32_d1(g, beta, s, a, b, work, cfg, st, conf);
-    if (g.d == 2) return interp_f32_d2(g, beta, s, a, b, work, cfg, st, conf);
-    return interp_f32_d3(g, beta, s, a, b, work, cfg, st, conf);
+    if (g.d == 1) return interp_f32_d1(g, beta, s, a, b, work, cfg, st, conf, bt);
+    if (g.d == 2) return interp_f32_d2(g, beta, s, a, b, work, cfg, st, conf, bt);
+    return interp_f32_d3(g, beta, s, a, b, work, cfg, st, conf, bt);
   }
-  if (g.d == 1) return interp_f64_d1(g, beta, s, a, b, work, cfg, st, conf);
-  if (g.d == 2) return interp_f64_d2(g, beta, s, a, b, work, cfg, st, conf);
-  return interp_f64_d3(g, beta, s, a, b, work, cfg, st, conf);
+  if (g.d == 1) return interp_f64_d1(g, beta, s, a, b, work, cfg, st, conf, bt);
+  if (g.d == 2) return interp_f64_d2(g, beta, s, a, b, work, cfg, st, conf, bt);
+  return interp_f64_d3(g, beta, s, a, b, work, cfg, st, conf, bt);
 }
 
 static cudaError_t configure(bool spread, bool dbl, const Geom& g, int threads, LaunchCfg* cfg) {
@@ -258,7 +258,8 @@ static cudaError_t configure(bool spread, bool dbl, const Geom& g, int threads, 
   cfg->smem = spread ? spread_smem_bytes(dbl, g, threads) : interp_smem_bytes(dbl, g, threads);
   cfg->blocks = 0;
   Sorted s{};
-  cudaError_t e = si_dispatch(spread, dbl, g, 0.0, s, nullptr, nullptr, nullptr, *cfg, nullptr, true);
+  BatchTable none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  cudaError_t e = si_dispatch(spread, dbl, g, 0.0, s, nullptr, nullptr, nullptr, *cfg, nullptr, true, none);
   if (e != cudaSuccess) return e;
   int per_sm = cfg->blocks, dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -275,12 +276,12 @@ cudaError_t interp_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg) 
   return configure(false, dbl, g, threads, cfg);
 }
 cudaError_t launch_spread(bool dbl, const Geom& g, double beta, const Sorted& s, const void* c,
-                          void* grid, int* work, const LaunchCfg& cfg, cudaStream_t st) {
-  return si_dispatch(true, dbl, g, beta, s, c, grid, work, cfg, st, false);
+                          void* grid, int* work, const LaunchCfg& cfg, cudaStream_t st, const BatchTable& bt) {
+  return si_dispatch(true, dbl, g, beta, s, c, grid, work, cfg, st, false, bt);
 }
 cudaError_t launch_interp(bool dbl, const Geom& g, double beta, const Sorted& s, const void* grid,
-                          void* c, int* work, const LaunchCfg& cfg, cudaStream_t st) {
-  return si_dispatch(false, dbl, g, beta, s, grid, c, work, cfg, st, false);
+                          void* c, int* work, const LaunchCfg& cfg, cudaStream_t st, const BatchTable& bt) {
+  return si_dispatch(false, dbl, g, beta, s, grid, c, work, cfg, st, false, bt);
 }
 
 }  // namespace nufft
@@ -554,6 +555,386 @@ int nufft_plan_info(nufft_plan p, int* w, double* beta, int64_t* n, int* bins, i
     }
   }
   return NUFFT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+// Many independent transforms of one type, dimension, precision and eps with
+// their own mode counts.  All transforms share one bin shape (so the spread /
+// interp kernels run one tile size), their fine grids sit in one allocation
+// grouped by size (one batched cuFFT plan per size), and every step is one
+// launch over all transforms: the binning kernels find a point's transform
+// from the point offsets, the spread / interp kernels a subproblem's from the
+// bin offsets, the correction kernels a row's from the row offsets.  The
+// execute sequence is captured once in a CUDA graph and replayed.
+
+struct nufft_batch_s {
+  int type = 0, dim = 0, isign = 0, prec = 0;
+  bool dbl = false;
+  size_t csize = 8;
+  nufft_opts opts;
+  int B = 0;
+  int w = 0;
+  double beta = 0;
+  Geom g;  // shared: d, w, half, B, T, ntile, maxsub
+  std::vector<BatchGeom> hg;
+  BatchGeom* bg = nullptr;
+  int* boff = nullptr;
+  int* poff = nullptr;
+  long long* growoff = nullptr;
+  long long* mrowoff = nullptr;
+  int total_bins = 0;
+  long long total_grid = 0, total_modes = 0, total_grow = 0, total_mrow = 0;
+  int max_grow = 1, max_mrow = 1;
+  void* grid = nullptr;
+  void* pk = nullptr;
+  struct SizeClass {
+    int n[3];
+    int count;
+    long long goff;
+    cufftHandle plan;
+    bool ok;
+  };
+  std::vector<SizeClass> classes;
+  int* bin_count = nullptr;
+  int* bin_start = nullptr;
+  int* sub_first = nullptr;
+  int* cursor = nullptr;
+  int* small = nullptr;  // [0] error word, [1] nsub, [2] work counter
+  int64_t M = -1, Mcap = 0, subcap = 0;
+  void* rec = nullptr;
+  int* sub_bin = nullptr;
+  int* sub_pt0 = nullptr;
+  int* sub_cnt = nullptr;
+  std::vector<int> hpoff;
+  LaunchCfg cfg{0, 0, 0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};  // c, f, rec, sub arrays the graph was built for
+};
+
+namespace {
+
+BatchTable table_of(nufft_batch p) {
+  return BatchTable{p->bg, p->boff, p->poff, p->growoff, p->mrowoff, p->B};
+}
+
+int batch_fail(nufft_batch p, int code) {
+  nufft_batch_destroy(p);
+  return code;
+}
+
+// The execute sequence, enqueued on the plan's stream.
+int batch_enqueue(nufft_batch p, void* c, void* f) {
+  const BatchTable bt = table_of(p);
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1};
+  const int dir = p->isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
+  const int modeord = p->opts.modeord ? 1 : 0;
+  auto ffts = [&]() -> int {
+    for (auto& cl : p->classes) {
+      char* gp = (char*)p->grid + (size_t)cl.goff * p->csize;
+      cufftResult r = p->dbl ? cufftExecZ2Z(cl.plan, (cufftDoubleComplex*)gp, (cufftDoubleComplex*)gp, dir)
+                             : cufftExecC2C(cl.plan, (cufftComplex*)gp, (cufftComplex*)gp, dir);
+      if (r != CUFFT_SUCCESS) return NUFFT_ERR_CUFFT;
+    }
+    return NUFFT_OK;
+  };
+  if (p->type == 1) {
+    CUDA_TRY(cudaMemsetAsync(p->grid, 0, (size_t)p->total_grid * p->csize, p->stream));
+    if (p->M > 0) {
+      CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
+      CUDA_TRY(launch_spread(p->dbl, p->g, p->beta, s, c, p->grid, p->small + 2, p->cfg, p->stream, bt));
+    }
+    int r = ffts();
+    if (r != NUFFT_OK) return r;
+    CUDA_TRY(launch_deconv_batch(p->dbl, p->dim, modeord, p->total_mrow, p->max_mrow, bt, p->grid, f, p->pk, p->stream));
+  } else {
+    CUDA_TRY(launch_precorrect_batch(p->dbl, p->dim, modeord, p->total_grow, p->max_grow, bt, f, p->grid, p->pk,
+                                     p->stream));
+    int r = ffts();
+    if (r != NUFFT_OK) return r;
+    if (p->M > 0) {
+      CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
+      CUDA_TRY(launch_interp(p->dbl, p->g, p->beta, s, p->grid, c, p->small + 2, p->cfg, p->stream, bt));
+    }
+  }
+  return NUFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int isign, double eps, int prec,
+                         void* stream, const nufft_opts* opts, nufft_batch* out) {
+  if (!out) return NUFFT_ERR_BAD_ARG;
+  *out = nullptr;
+  if ((type != 1 && type != 2) || (isign != 1 && isign != -1) || B < 1 || !nmodes || dim < 1 || dim > 3)
+    return NUFFT_ERR_BAD_ARG;
+  nufft_batch p = new (std::nothrow) nufft_batch_s();
+  if (!p) return NUFFT_ERR_ALLOC;
+  p->type = type;
+  p->dim = dim;
+  p->isign = isign;
+  p->prec = prec;
+  p->dbl = (prec == NUFFT_C128);
+  p->csize = p->dbl ? 16 : 8;
+  p->B = B;
+  if (opts) p->opts = *opts;
+  else nufft_default_opts(&p->opts);
+  p->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&p->device) != cudaSuccess) return batch_fail(p, NUFFT_ERR_CUDA);
+  // per-transform parameters; the widest grid sets the shared bin shape
+  std::vector<int64_t> n((size_t)B * 3, 1);
+  int warn = NUFFT_OK;
+  for (int t = 0; t < B; ++t) {
+    int w;
+    double beta;
+    int st = choose_params_impl(dim, nmodes + (size_t)t * dim, eps, prec, &w, &beta, &n[(size_t)t * 3]);
+    if (st < 0) return batch_fail(p, st);
+    warn = st;
+    p->w = w;
+    p->beta = beta;
+    for (int i = 0; i < dim; ++i)
+      if (nmodes[(size_t)t * dim + i] > (1 << 29) || n[(size_t)t * 3 + i] > (1 << 30)) return batch_fail(p, NUFFT_ERR_TOO_BIG);
+  }
+  Geom& g = p->g;
+  g.d = dim;
+  g.w = p->w;
+  g.half = p->w / 2;
+  g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
+  for (int i = 0; i < 3; ++i) {
+    int64_t mx = 1;
+    for (int t = 0; t < B; ++t) mx = std::max(mx, n[(size_t)t * 3 + i]);
+    g.n[i] = (int)mx;
+  }
+  choose_bins(g, p->dbl, p->opts);
+  // size classes (one batched FFT each), grid offsets by class, everything else in transform order
+  p->hg.resize(B);
+  std::vector<int> cls(B);
+  for (int t = 0; t < B; ++t) {
+    int k = -1;
+    for (size_t c = 0; c < p->classes.size(); ++c)
+      if (p->classes[c].n[0] == n[(size_t)t * 3] && p->classes[c].n[1] == n[(size_t)t * 3 + 1] &&
+          p->classes[c].n[2] == n[(size_t)t * 3 + 2])
+        k = (int)c;
+    if (k < 0) {
+      nufft_batch_s::SizeClass sc;
+      for (int i = 0; i < 3; ++i) sc.n[i] = (int)n[(size_t)t * 3 + i];
+      sc.count = 0;
+      sc.goff = 0;
+      sc.ok = false;
+      p->classes.push_back(sc);
+      k = (int)p->classes.size() - 1;
+    }
+    cls[t] = k;
+    p->classes[k].count++;
+  }
+  long long goff = 0;
+  for (auto& c : p->classes) {
+    c.goff = goff;
+    goff += (long long)c.count * c.n[0] * c.n[1] * c.n[2];
+  }
+  p->total_grid = goff;
+  std::vector<int> seen(p->classes.size(), 0);
+  std::vector<int> hboff(B + 1, 0);
+  std::vector<long long> hgrow(B + 1, 0), hmrow(B + 1, 0);
+  long long moff = 0, pkoff = 0;
+  int boffc = 0;
+  for (int t = 0; t < B; ++t) {
+    BatchGeom& tg = p->hg[t];
+    Geom gt = g;
+    for (int i = 0; i < 3; ++i) gt.n[i] = (int)n[(size_t)t * 3 + i];
+    finish_geom(gt);
+    int64_t Nt = 1;
+    for (int i = 0; i < 3; ++i) {
+      tg.n[i] = gt.n[i];
+      tg.nb[i] = gt.nb[i];
+      tg.ns[i] = gt.ns[i];
+      tg.sb[i] = gt.sb[i];
+      tg.lsb[i] = gt.lsb[i];
+      tg.N[i] = i < dim ? (int)nmodes[(size_t)t * dim + i] : 1;
+      Nt *= tg.N[i];
+      tg.fs[i] = (double)tg.n[i] / 6.283185307179586476925286766559;
+      tg.fs_hi[i] = (float)tg.fs[i];
+      tg.fs_lo[i] = (float)(tg.fs[i] - (double)tg.fs_hi[i]);
+      tg.pkoff[i] = (int)pkoff;
+      pkoff += tg.N[i];
+    }
+    tg.nbins = gt.nbins;
+    tg.boff = boffc;
+    hboff[t] = boffc;
+    boffc += gt.nbins;
+    const auto& c = p->classes[cls[t]];
+    tg.goff = c.goff + (long long)seen[cls[t]]++ * c.n[0] * c.n[1] * c.n[2];
+    tg.moff = moff;
+    moff += Nt;
+    tg.growoff = hgrow[t];
+    hgrow[t + 1] = hgrow[t] + (long long)tg.n[1] * tg.n[2];
+    tg.mrowoff = hmrow[t];
+    hmrow[t + 1] = hmrow[t] + (long long)tg.N[1] * tg.N[2];
+    p->max_grow = std::max(p->max_grow, tg.n[0]);
+    p->max_mrow = std::max(p->max_mrow, tg.N[0]);
+  }
+  if ((long long)boffc >= (1LL << 31) - 1) return batch_fail(p, NUFFT_ERR_TOO_BIG);
+  hboff[B] = boffc;
+  p->total_bins = boffc;
+  p->total_modes = moff;
+  p->total_grow = hgrow[B];
+  p->total_mrow = hmrow[B];
+  // correction factors of every transform and dimension, one array
+  std::vector<double> pkh((size_t)pkoff, 1.0);
+  for (int t = 0; t < B; ++t)
+    for (int i = 0; i < dim; ++i)
+      if (correction_impl(p->hg[t].N[i], p->hg[t].n[i], p->w, p->beta, &pkh[p->hg[t].pkoff[i]]) != NUFFT_OK)
+        return batch_fail(p, NUFFT_ERR_BAD_ARG);
+  const size_t rs = p->dbl ? 8 : 4;
+  if (dev_alloc(&p->grid, (size_t)p->total_grid * p->csize) != cudaSuccess ||
+      dev_alloc(&p->pk, pkh.size() * rs) != cudaSuccess ||
+      dev_alloc(&p->bg, sizeof(BatchGeom) * (size_t)B) != cudaSuccess ||
+      dev_alloc(&p->boff, sizeof(int) * (size_t)(B + 1)) != cudaSuccess ||
+      dev_alloc(&p->poff, sizeof(int) * (size_t)(B + 1)) != cudaSuccess ||
+      dev_alloc(&p->growoff, sizeof(long long) * (size_t)(B + 1)) != cudaSuccess ||
+      dev_alloc(&p->mrowoff, sizeof(long long) * (size_t)(B + 1)) != cudaSuccess ||
+      dev_alloc(&p->bin_count, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
+      dev_alloc(&p->bin_start, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
+      dev_alloc(&p->sub_first, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
+      dev_alloc(&p->cursor, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
+      dev_alloc(&p->small, sizeof(int) * 4) != cudaSuccess)
+    return batch_fail(p, NUFFT_ERR_ALLOC);
+  bool okc = true;
+  if (p->dbl) {
+    okc &= cudaMemcpy(p->pk, pkh.data(), pkh.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+  } else {
+    std::vector<float> pf(pkh.begin(), pkh.end());
+    okc &= cudaMemcpy(p->pk, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  okc &= cudaMemcpy(p->bg, p->hg.data(), sizeof(BatchGeom) * (size_t)B, cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(p->boff, hboff.data(), sizeof(int) * (size_t)(B + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(p->growoff, hgrow.data(), sizeof(long long) * (size_t)(B + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemcpy(p->mrowoff, hmrow.data(), sizeof(long long) * (size_t)(B + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+  okc &= cudaMemset(p->small, 0, sizeof(int) * 4) == cudaSuccess;
+  if (!okc) return batch_fail(p, NUFFT_ERR_CUDA);
+  int threads = p->opts.threads > 0 ? p->opts.threads : 256;
+  if (threads % 32 != 0 || threads > 256) return batch_fail(p, NUFFT_ERR_BAD_ARG);
+  cudaError_t e = (type == 1) ? spread_config(p->dbl, g, threads, &p->cfg) : interp_config(p->dbl, g, threads, &p->cfg);
+  if (e != cudaSuccess) return batch_fail(p, NUFFT_ERR_CUDA);
+  for (auto& c : p->classes) {
+    int nn[3];
+    for (int i = 0; i < dim; ++i) nn[i] = c.n[dim - 1 - i];
+    const int dist = c.n[0] * c.n[1] * c.n[2];
+    if (cufftPlanMany(&c.plan, dim, nn, nullptr, 1, dist, nullptr, 1, dist, p->dbl ? CUFFT_Z2Z : CUFFT_C2C,
+                      c.count) != CUFFT_SUCCESS)
+      return batch_fail(p, NUFFT_ERR_CUFFT);
+    c.ok = true;
+    if (cufftSetStream(c.plan, p->stream) != CUFFT_SUCCESS) return batch_fail(p, NUFFT_ERR_CUFFT);
+  }
+  *out = p;
+  return warn;
+}
+
+int nufft_batch_setpts(nufft_batch p, const int64_t* offsets, const void* x, const void* y, const void* z) {
+  if (!p || !offsets || offsets[0] != 0) return NUFFT_ERR_BAD_ARG;
+  for (int t = 0; t < p->B; ++t)
+    if (offsets[t + 1] < offsets[t]) return NUFFT_ERR_BAD_ARG;
+  const int64_t M = offsets[p->B];
+  if (M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_TOO_BIG;
+  if (M > 0 && (!x || (p->dim > 1 && !y) || (p->dim > 2 && !z))) return NUFFT_ERR_BAD_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  p->hpoff.assign(offsets, offsets + p->B + 1);
+  // pageable source: the copy is staged before the call returns
+  if (cudaMemcpyAsync(p->poff, p->hpoff.data(), sizeof(int) * (size_t)(p->B + 1), cudaMemcpyHostToDevice, p->stream) !=
+      cudaSuccess)
+    return NUFFT_ERR_CUDA;
+  if (M > p->Mcap) {
+    cudaFree(p->rec);
+    p->rec = nullptr;
+    p->Mcap = 0;
+    if (dev_alloc(&p->rec, (p->dbl ? sizeof(RecD) : sizeof(RecF)) * (size_t)M) != cudaSuccess) return NUFFT_ERR_ALLOC;
+    p->Mcap = M;
+  }
+  int64_t need = std::min<int64_t>(p->total_bins, M) + M / p->g.maxsub + 1;
+  if (need > p->subcap) {
+    cudaFree(p->sub_bin);
+    cudaFree(p->sub_pt0);
+    cudaFree(p->sub_cnt);
+    p->sub_bin = p->sub_pt0 = p->sub_cnt = nullptr;
+    p->subcap = 0;
+    if (dev_alloc(&p->sub_bin, sizeof(int) * (size_t)need) != cudaSuccess ||
+        dev_alloc(&p->sub_pt0, sizeof(int) * (size_t)need) != cudaSuccess ||
+        dev_alloc(&p->sub_cnt, sizeof(int) * (size_t)need) != cudaSuccess)
+      return NUFFT_ERR_ALLOC;
+    p->subcap = need;
+  }
+  FoldConst fc = make_fold_const(p->g);
+  cudaError_t e = launch_setpts(p->dbl, p->g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
+                                p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1,
+                                p->small + 0, p->stream, nullptr, table_of(p), p->total_bins);
+  if (e != cudaSuccess) return NUFFT_ERR_CUDA;
+  p->M = M;
+  return NUFFT_OK;
+}
+
+int nufft_batch_execute(nufft_batch p, void* c, void* f) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  if (p->M < 0) return NUFFT_ERR_NOT_SET;
+  if (!f || (p->M > 0 && !c)) return NUFFT_ERR_BAD_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  const void* key[4] = {c, f, p->rec, p->sub_bin};
+  bool same = p->gexec != nullptr;
+  for (int i = 0; i < 4; ++i) same = same && key[i] == p->gkey[i];
+  if (!same) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    // capture the execute sequence once; replay it while the pointers stay the same
+    cudaGraph_t graph = nullptr;
+    if (p->stream && cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int r = batch_enqueue(p, c, f);
+      cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+      if (r == NUFFT_OK && ce == cudaSuccess && graph &&
+          cudaGraphInstantiate(&p->gexec, graph, 0) == cudaSuccess) {
+        for (int i = 0; i < 4; ++i) p->gkey[i] = key[i];
+      } else {
+        p->gexec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+    }
+    if (!p->gexec) return batch_enqueue(p, c, f);  // no capture on the legacy default stream
+  }
+  return cudaGraphLaunch(p->gexec, p->stream) == cudaSuccess ? NUFFT_OK : NUFFT_ERR_CUDA;
+}
+
+int nufft_batch_destroy(nufft_batch p) {
+  if (!p) return NUFFT_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(p->device);
+  cudaStreamSynchronize(p->stream);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  for (auto& c : p->classes)
+    if (c.ok) cufftDestroy(c.plan);
+  void* bufs[] = {p->grid, p->pk, p->bg, p->boff, p->poff, p->growoff, p->mrowoff, p->bin_count, p->bin_start,
+                  p->sub_first, p->cursor, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  cudaSetDevice(dev);
+  delete p;
+  return NUFFT_OK;
+}
+
+int nufft_batch_get_status(nufft_batch p) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, p->small, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NUFFT_ERR_CUDA;
+  if (err != 0 && cudaMemset(p->small, 0, sizeof(int)) != cudaSuccess) return NUFFT_ERR_CUDA;
+  return err;
 }
 
 }  // extern "C"

@@ -295,18 +295,43 @@ struct MinBlocks {
   static constexpr int value = sizeof(T) == 4 ? 4 : 2;
 };
 
+// Thread 0 takes the next subproblem and puts its geometry in shared memory:
+// for a batch, the subproblem's transform, its grid offset and its bin id
+// within that transform.  Returns false when the work list is exhausted.
+__device__ __forceinline__ void next_subproblem(const Geom& g, const Sorted& s, const BatchTable& bt, int* work,
+                                                int* s_sub, int* s_bin, long long* s_goff, Geom* s_geo) {
+  const int sub = atomicAdd(work, 1);
+  *s_sub = sub;
+  if (sub < *s.nsub) {
+    int bin = s.sub_bin[sub];
+    *s_geo = g;
+    long long goff = 0;
+    if (bt.B > 0) {
+      const int t = batch_find(bt.boff, bt.B, bin);
+      const BatchGeom tg = bt.bg[t];
+      batch_apply(*s_geo, tg);
+      bin -= tg.boff;
+      goff = tg.goff;
+    }
+    *s_bin = bin;
+    *s_goff = goff;
+  }
+}
+
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T kpar, Sorted s,
                                                 const typename Traits<T>::C* __restrict__ c,
                                                 typename Traits<T>::C* __restrict__ grid,
-                                                int* __restrict__ work) {
+                                                int* __restrict__ work, BatchTable bt) {
   using C = typename Traits<T>::C;
   using Rec = typename Traits<T>::Rec;
   using F = Fixed<T>;
   using I = typename F::I;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_SPREAD];
-  __shared__ int s_sub;
+  __shared__ int s_sub, s_bin;
+  __shared__ long long s_goff;
+  __shared__ Geom s_geo;
   __shared__ I s_maxbits;
 
   const int ntile = g.ntile, maxsub = g.maxsub;
@@ -319,14 +344,14 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T k
 
   for (;;) {
     if (threadIdx.x == 0) {
-      s_sub = atomicAdd(work, 1);
+      next_subproblem(g, s, bt, work, &s_sub, &s_bin, &s_goff, &s_geo);
       s_maxbits = 0;
     }
     if (threadIdx.x < NRES_SPREAD) hist[threadIdx.x] = 0;
     __syncthreads();
     const int sub = s_sub;
     if (sub >= *s.nsub) break;
-    const int bin = s.sub_bin[sub], p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+    const int bin = s_bin, p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
 
     for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
       tre[t] = 0;
@@ -426,8 +451,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T k
     // add the tile into the fine grid, wrapping periodically; rows of the
     // tile are spread over the warps, a warp's lanes walk along x
     int org[3];
-    tile_origin(g, bin, org);
-    flush_tile<T>(g, org, tre, tim, inv, grid);
+    tile_origin(s_geo, bin, org);
+    flush_tile<T>(s_geo, org, tre, tim, inv, grid + s_goff);
     __syncthreads();
   }
 }
@@ -437,12 +462,14 @@ template <typename T, int D, int W>
 __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T kpar, Sorted s,
                                                 const typename Traits<T>::C* __restrict__ grid,
                                                 typename Traits<T>::C* __restrict__ c,
-                                                int* __restrict__ work) {
+                                                int* __restrict__ work, BatchTable bt) {
   using C = typename Traits<T>::C;
   using Rec = typename Traits<T>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_INTERP];
-  __shared__ int s_sub;
+  __shared__ int s_sub, s_bin;
+  __shared__ long long s_goff;
+  __shared__ Geom s_geo;
 
   const int ntile = g.ntile, maxsub = g.maxsub;
   C* tile = reinterpret_cast<C*>(smem);
@@ -451,24 +478,26 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T k
   const int T0 = g.T[0], T01 = g.T[0] * g.T[1];
 
   for (;;) {
-    if (threadIdx.x == 0) s_sub = atomicAdd(work, 1);
+    if (threadIdx.x == 0) next_subproblem(g, s, bt, work, &s_sub, &s_bin, &s_goff, &s_geo);
     if (threadIdx.x < NRES_INTERP) hist[threadIdx.x] = 0;
     __syncthreads();
     const int sub = s_sub;
     if (sub >= *s.nsub) break;
-    const int bin = s.sub_bin[sub], p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+    const int bin = s_bin, p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
 
     // fetch the tile (bin + halo) from the fine grid, wrapping periodically
     int org[3];
-    tile_origin(g, bin, org);
+    tile_origin(s_geo, bin, org);
     const int nrows = ntile / T0;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int n0 = s_geo.n[0], n1 = s_geo.n[1], n2 = s_geo.n[2];
+    const C* gridt = grid + s_goff;
     for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
       const int t1 = row % g.T[1], t2 = row / g.T[1];
-      const long long gy = wrap_idx(org[1] + t1, g.n[1]);
-      const long long gz = wrap_idx(org[2] + t2, g.n[2]);
-      const C* grow = grid + (gz * g.n[1] + gy) * (long long)g.n[0];
-      for (int t0 = lane; t0 < T0; t0 += 32) cp_async_elem(tile + row * T0 + t0, grow + wrap_idx(org[0] + t0, g.n[0]));
+      const long long gy = wrap_idx(org[1] + t1, n1);
+      const long long gz = wrap_idx(org[2] + t2, n2);
+      const C* grow = gridt + (gz * n1 + gy) * (long long)n0;
+      for (int t0 = lane; t0 < T0; t0 += 32) cp_async_elem(tile + row * T0 + t0, grow + wrap_idx(org[0] + t0, n0));
     }
     cp_async_commit();
     // records in batches of four per thread while the tile copies are in flight
@@ -565,7 +594,8 @@ inline double kernel_param<double>(double beta) {
 
 template <typename T, int D, int W>
 cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* c, void* grid,
-                       int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only) {
+                       int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
+                       const BatchTable& bt) {
   auto kern = k_spread<T, D, W>;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -578,13 +608,14 @@ cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* 
   }
   kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
       g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
-      reinterpret_cast<typename Traits<T>::C*>(grid), work);
+      reinterpret_cast<typename Traits<T>::C*>(grid), work, bt);
   return cudaGetLastError();
 }
 
 template <typename T, int D, int W>
 cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* grid, void* c,
-                       int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only) {
+                       int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
+                       const BatchTable& bt) {
   auto kern = k_interp<T, D, W>;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -597,40 +628,40 @@ cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* 
   }
   kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
       g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
-      reinterpret_cast<typename Traits<T>::C*>(c), work);
+      reinterpret_cast<typename Traits<T>::C*>(c), work, bt);
   return cudaGetLastError();
 }
 
 // w -> template dispatch for one (precision, dimension)
 #define NUFFT_W_CASES(FN, T, D)                                             \
   switch (g.w) {                                                            \
-    case 2: return FN<T, D, 2>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 3: return FN<T, D, 3>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 4: return FN<T, D, 4>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 5: return FN<T, D, 5>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 6: return FN<T, D, 6>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 7: return FN<T, D, 7>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 8: return FN<T, D, 8>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 9: return FN<T, D, 9>(g, beta, s, a, b, work, cfg, st, conf);      \
-    case 10: return FN<T, D, 10>(g, beta, s, a, b, work, cfg, st, conf);    \
-    case 11: return FN<T, D, 11>(g, beta, s, a, b, work, cfg, st, conf);    \
-    case 12: return FN<T, D, 12>(g, beta, s, a, b, work, cfg, st, conf);    \
-    case 13: return FN<T, D, 13>(g, beta, s, a, b, work, cfg, st, conf);    \
-    case 14: return FN<T, D, 14>(g, beta, s, a, b, work, cfg, st, conf);    \
-    case 15: return FN<T, D, 15>(g, beta, s, a, b, work, cfg, st, conf);    \
-    case 16: return FN<T, D, 16>(g, beta, s, a, b, work, cfg, st, conf);    \
+    case 2: return FN<T, D, 2>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 3: return FN<T, D, 3>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 4: return FN<T, D, 4>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 5: return FN<T, D, 5>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 6: return FN<T, D, 6>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 7: return FN<T, D, 7>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 8: return FN<T, D, 8>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 9: return FN<T, D, 9>(g, beta, s, a, b, work, cfg, st, conf, bt);      \
+    case 10: return FN<T, D, 10>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
+    case 11: return FN<T, D, 11>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
+    case 12: return FN<T, D, 12>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
+    case 13: return FN<T, D, 13>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
+    case 14: return FN<T, D, 14>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
+    case 15: return FN<T, D, 15>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
+    case 16: return FN<T, D, 16>(g, beta, s, a, b, work, cfg, st, conf, bt);    \
     default: return cudaErrorInvalidValue;                                  \
   }
 
 #define NUFFT_DEFINE_SI(P, T, D)                                                                   \
   cudaError_t spread_##P##_d##D(const Geom& g, double beta, const Sorted& s, const void* a,       \
                                 void* b, int* work, const LaunchCfg& cfg, cudaStream_t st,         \
-                                bool conf) {                                                       \
+                                bool conf, const BatchTable& bt) {                                 \
     NUFFT_W_CASES(run_spread, T, D)                                                                \
   }                                                                                                \
   cudaError_t interp_##P##_d##D(const Geom& g, double beta, const Sorted& s, const void* a,       \
                                 void* b, int* work, const LaunchCfg& cfg, cudaStream_t st,         \
-                                bool conf) {                                                       \
+                                bool conf, const BatchTable& bt) {                                 \
     NUFFT_W_CASES(run_interp, T, D)                                                                \
   }
 
