@@ -73,10 +73,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=300_000)
-    ap.add_argument("--workload", default="3d", choices=["3d", "batched2d"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "batched2d", "serving"],
                     help="3d: the 3D type-1/type-2 workload (default); batched2d: many uneven 2D type-2 "
-                         "transforms, batched plan against one plan per transform")
+                         "transforms, batched plan against one plan per transform; serving: a Poisson stream "
+                         "of mixed requests through the request loop against the plain plan path")
     ap.add_argument("--B", type=int, default=1024, help="transforms in the batched2d workload")
+    ap.add_argument("--requests", type=int, default=2000, help="requests in the serving trace")
+    ap.add_argument("--rate", type=float, default=2000.0, help="mean arrivals per second in the serving trace")
+    ap.add_argument("--slots", type=int, default=8, help="execution slots of the request loop")
+    ap.add_argument("--serve-budget-gb", type=int, default=64, help="device-memory budget of the request loop")
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving summary out of the 3d line")
     return ap.parse_args()
 
 
@@ -463,6 +469,161 @@ def run_batched2d(args):
     return 0
 
 
+def _pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def run_serving(args):
+    """The serving trace (nufft_inputs.serving_trace: Poisson arrivals at --rate of
+    mixed 2D/3D type-1/type-2 complex64 requests with M log-uniform in [1e4, 1e7],
+    20 % least-squares gradient requests at 3D N = 64^3, M = 1e5) through
+    (a) the request loop (Server: --slots slots, resident plan entries) and
+    (b) the plain path: one request at a time through cached Plans (gradient
+    requests through the autograd functions), synchronising after each.
+    Open loop: each request is submitted at its arrival time; latency = device
+    completion - arrival.  Burst: the whole trace submitted at once; points/s =
+    sum of M / makespan.  Inputs are slices of pools resident in HBM; each arm
+    runs the trace once untimed first (plan creation)."""
+    import numpy as np
+    import torch
+
+    import nufft_inputs as I
+    from paper_1808_06736_gb300 import autograd as AG
+    from paper_1808_06736_gb300 import serve as S
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pool = 10_000_000
+    trace = I.serving_trace(8000, args.requests, args.rate, pool)
+    X = I.torch_points(8001, pool, 3, "uniform", dev, torch.float32)
+    C = I.torch_complex_normal(8002, pool, dev, torch.complex64)
+    maxn = max(int(np.prod(q["modes"])) for q in trace)
+    F = I.torch_complex_normal(8003, maxn, dev, torch.complex64)
+    Y = I.torch_complex_normal(8004, 100_000, dev, torch.complex64)
+    torch.cuda.synchronize()
+    clock = S.nufft_server_clock
+    total_pts = sum(q["M"] for q in trace)
+
+    def inputs(q):
+        M, o = q["M"], q["off"]
+        xs = [X[d][o:o + M] for d in range(q["d"])]
+        f = F[: int(np.prod(q["modes"]))].view(tuple(reversed(q["modes"])))
+        return xs, f, C[o:o + M], Y[:M]
+
+    def submit(srv, q, tag):
+        xs, f, c, y = inputs(q)
+        if q["kind"] == 1:
+            return srv.type1(xs, c, q["modes"], eps=q["eps"], isign=q["isign"], tag=tag)
+        if q["kind"] == 2:
+            return srv.type2(xs, f, eps=q["eps"], isign=q["isign"], tag=tag)
+        return srv.lsq_grad(xs, f, y, eps=q["eps"], isign=q["isign"], tag=tag)
+
+    def collect(srv, n, got):
+        t_end = time.time() + 600
+        while len(got) < n and time.time() < t_end:
+            for c in srv.poll(512, 0.05):
+                got[c.tag] = c
+        return got
+
+    srv = S.Server(budget_bytes=args.serve_budget_gb << 30, max_inflight=args.slots)
+
+    def served_burst():
+        t0 = clock()
+        for i, q in enumerate(trace):
+            submit(srv, q, i)
+        got = collect(srv, len(trace), {})
+        assert all(c.status == 0 for c in got.values()), "served request failed"
+        return max(c.t_done for c in got.values()) - t0
+
+    served_burst()  # untimed: creates the resident entries
+    mk_served = served_burst()
+    t0 = clock() + 0.05
+    got = {}
+    for i, q in enumerate(trace):
+        target = t0 + q["t"]
+        while True:
+            now = clock()
+            if now >= target:
+                break
+            for c in srv.poll(512, min(target - now, 0.001)):
+                got[c.tag] = c
+        submit(srv, q, i)
+    collect(srv, len(trace), got)
+    st = srv.stats()
+    srv.close()
+    assert all(c.status == 0 for c in got.values()), "served request failed"
+    lat_s = [(got[i].t_done - (t0 + q["t"])) * 1e3 for i, q in enumerate(trace)]
+    wait_s = [(got[i].t_admit - (t0 + q["t"])) * 1e3 for i, q in enumerate(trace)]
+
+    cache = AG.PlanCache()
+
+    def run_plain(q):
+        xs, f, c, y = inputs(q)
+        if q["kind"] == 1:
+            p = cache.get(1, q["modes"], q["eps"], q["isign"], torch.complex64, dev)
+            p.setpts(*xs)
+            p.execute(c)
+        elif q["kind"] == 2:
+            p = cache.get(2, q["modes"], q["eps"], q["isign"], torch.complex64, dev)
+            p.setpts(*xs)
+            p.execute(f)
+        else:
+            xg = torch.stack(xs).requires_grad_()
+            fg = f.detach().clone().requires_grad_()
+            cc = AG.nufft_type2(xg, fg, eps=q["eps"], isign=q["isign"], cache=cache)
+            loss = ((cc - y).abs() ** 2).sum()
+            loss.backward()
+        torch.cuda.synchronize()
+
+    for q in trace:  # untimed: creates the plans
+        run_plain(q)
+    t = clock()
+    for q in trace:
+        run_plain(q)
+    mk_plain = clock() - t
+    t0 = clock() + 0.05
+    lat_p = []
+    for q in trace:
+        target = t0 + q["t"]
+        while clock() < target:
+            time.sleep(max(0.0, min(0.0005, target - clock())))
+        run_plain(q)
+        lat_p.append((clock() - target) * 1e3)
+    cache.clear()
+    n3 = sum(1 for q in trace if q["kind"] == 3)
+    return {
+        "requests": len(trace), "rate_per_s": args.rate, "gradient_requests": n3,
+        "points_total": total_pts, "offered_pts_per_s": total_pts / trace[-1]["t"],
+        "served": {"p50_ms": _pct(lat_s, 50), "p99_ms": _pct(lat_s, 99), "mean_ms": statistics.mean(lat_s),
+                   "p99_queue_ms": _pct(wait_s, 99), "burst_pts_per_s": total_pts / mk_served,
+                   "burst_makespan_s": mk_served, "slots": args.slots, "budget_gb": args.serve_budget_gb,
+                   "entries_created": st["entries_created"], "entries_evicted": st["entries_evicted"],
+                   "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"]},
+        "plain": {"p50_ms": _pct(lat_p, 50), "p99_ms": _pct(lat_p, 99), "mean_ms": statistics.mean(lat_p),
+                  "burst_pts_per_s": total_pts / mk_plain, "burst_makespan_s": mk_plain,
+                  "path": "cached Plan per request shape, one request at a time, synchronised"},
+        "burst_throughput_vs_plain": mk_plain / mk_served,
+        "points": "each request counts its M points once (a gradient request runs 2 + d transforms on them)",
+    }
+
+
+def run_serving_line(args):
+    r = run_serving(args)
+    line = {"metric": "served p50/p99 latency (ms) of mixed type-1/2 requests, Poisson %g req/s" % args.rate,
+            "value": r["served"]["p99_ms"], "unit": "ms (p99)", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": r["served"]["burst_makespan_s"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving", "trace": "nufft_inputs.serving_trace(8000, %d, %g)"
+                       % (args.requests, args.rate)},
+            "serving": r}
+    print(json.dumps(line))
+    return 0
+
+
 def config_dict(args):
     return {"workload": "3D type 1 + type 2, N=%d^3 modes (fine grid %d^3), M=%d %s points, complex64, eps=%g"
                         % (args.N, 2 * args.N, args.M, args.kind, args.eps),
@@ -479,9 +640,14 @@ def main():
         return run_reference(args)
     if args.workload == "batched2d":
         return run_batched2d(args)
+    if args.workload == "serving":
+        return run_serving_line(args)
     r = run_cuda(args, ws, rank, local)
     if rank != 0:
         return 0
+    serving = None
+    if not args.no_serving and ws == 1:
+        serving = run_serving(args)
     cpu = None
     if not args.no_cpu:
         full, t_pts, t_fixed, _, cores = oracle_sample(args, args.cpu_sample)
@@ -493,7 +659,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args),
             "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
-            "gpu_launches": r["gpu_launches"], "kernels_ms": r["kernels_ms"]}
+            "gpu_launches": r["gpu_launches"], "kernels_ms": r["kernels_ms"], "serving": serving}
     print(json.dumps(line))
     return 0
 

@@ -52,6 +52,9 @@ extern "C" {
 #define NUFFT_ERR_CUFFT (-5)         /* cuFFT planning or execution failed */
 #define NUFFT_ERR_NOT_SET (-6)       /* nufft_execute before nufft_setpts */
 #define NUFFT_ERR_TOO_BIG (-7)       /* M >= 2^31, or a grid the index types cannot address */
+#define NUFFT_ERR_TIMEOUT (-8)       /* serving: a request was not done within the server's time limit */
+#define NUFFT_ERR_REJECTED (-9)      /* serving: a request needs more device memory than the whole budget */
+#define NUFFT_ERR_SHUTDOWN (-10)     /* serving: the server was destroyed before the request ran */
 
 typedef struct nufft_plan_s* nufft_plan;
 

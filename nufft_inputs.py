@@ -105,3 +105,35 @@ def torch_complex_normal(seed: int, n: int, device, dtype):
     real = torch.float32 if dtype == torch.complex64 else torch.float64
     v = torch.randn(n, 2, generator=g, device=device, dtype=real)
     return torch.view_as_complex(v).contiguous()
+
+
+# --------------------------------------------------------------- serving trace
+SERVING_2D_N = (64, 128, 256, 512, 1024)
+SERVING_3D_N = (64, 128, 256)
+
+
+def serving_trace(seed: int, n: int, rate: float, pool: int = 10_000_000):
+    """A mixed request stream: Poisson arrivals (mean ``rate`` per second) of
+    complex64 requests.  20 % are least-squares gradient requests (3D, N = 64^3,
+    M = 1e5); the rest are type 1 or type 2 (equally likely), 2D or 3D (equally
+    likely) with N_i drawn from SERVING_2D_N / SERVING_3D_N, M log-uniform in
+    [1e4, 1e7].  eps is 1e-3 or 1e-5 and the sign +1 or -1, each equally
+    likely.  ``off`` is where the request's points and strengths start in a
+    shared input pool of ``pool`` values."""
+    r = rng(seed)
+    t = np.cumsum(r.exponential(1.0 / rate, size=n))
+    out = []
+    for i in range(n):
+        eps = float(r.choice([1e-3, 1e-5]))
+        isign = int(r.choice([-1, 1]))
+        if r.random() < 0.2:
+            kind, d, modes, M = 3, 3, (64, 64, 64), 100_000
+        else:
+            kind = int(r.choice([1, 2]))
+            d = int(r.choice([2, 3]))
+            Nd = int(r.choice(SERVING_2D_N if d == 2 else SERVING_3D_N))
+            modes = (Nd,) * d
+            M = int(math.exp(r.uniform(math.log(1e4), math.log(1e7))))
+        off = int(r.integers(0, pool - M + 1))
+        out.append(dict(t=float(t[i]), kind=kind, d=d, modes=modes, M=M, eps=eps, isign=isign, off=off))
+    return out

@@ -208,4 +208,14 @@ cudaError_t launch_deconv_batch(bool dbl, int d, int modeord, long long nrows, i
 cudaError_t launch_precorrect_batch(bool dbl, int d, int modeord, long long nrows, int maxlen, const BatchTable& bt,
                                     const void* f, void* grid, const void* pk, cudaStream_t st);
 
+// --- plan internals used by the serving layer (plan.cu) ------------------------
+// Execute with the plan's grid, points and cuFFT plan but another type / sign
+// (type 1 on a type-2 plan is its adjoint when isign is flipped).
+int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f);
+int plan_set_stream(nufft_plan p, cudaStream_t s);
+int plan_reserve(nufft_plan p, int64_t mcap);  // point capacity without setting points
+size_t plan_device_bytes(nufft_plan p);
+int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes);
+int plan_modes(nufft_plan p, int64_t* N, int* dim);
+
 }  // namespace nufft

@@ -316,6 +316,9 @@ const char* nufft_strerror(int code) {
     case NUFFT_ERR_CUFFT: return "cuFFT error";
     case NUFFT_ERR_NOT_SET: return "execute called before setpts";
     case NUFFT_ERR_TOO_BIG: return "problem too large for the index types";
+    case NUFFT_ERR_TIMEOUT: return "request not done within the server's time limit";
+    case NUFFT_ERR_REJECTED: return "request needs more device memory than the server's budget";
+    case NUFFT_ERR_SHUTDOWN: return "server destroyed before the request ran";
     default: return "unknown status";
   }
 }
@@ -389,9 +392,10 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
     return fail(p, NUFFT_ERR_ALLOC);
   if (cudaMemset(p->small, 0, sizeof(int) * 4) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
 
-  cudaError_t e = (type == 1) ? spread_config(p->dbl, g, threads, &p->spread_cfg)
-                              : interp_config(p->dbl, g, threads, &p->interp_cfg);
-  if (e != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
+  // both launch shapes: the serving layer runs a plan's adjoint (type 1 on a type-2 plan)
+  if (spread_config(p->dbl, g, threads, &p->spread_cfg) != cudaSuccess ||
+      interp_config(p->dbl, g, threads, &p->interp_cfg) != cudaSuccess)
+    return fail(p, NUFFT_ERR_CUDA);
 
   // cuFFT: dimensions slowest first
   int nn[3];
@@ -450,6 +454,15 @@ int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const vo
 
 int nufft_execute(nufft_plan p, void* c, void* f) {
   if (!p) return NUFFT_ERR_BAD_ARG;
+  return nufft::plan_execute_as(p, p->type, p->isign, c, f);
+}
+
+}  // extern "C"
+
+namespace nufft {
+
+int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
   if (p->M < 0) return NUFFT_ERR_NOT_SET;
   if (!f || (p->M > 0 && !c)) return NUFFT_ERR_BAD_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
@@ -462,12 +475,12 @@ int nufft_execute(nufft_plan p, void* c, void* f) {
     mg.N[i] = (int)p->N[i];
     mg.n[i] = g.n[i];
   }
-  const int dir = p->isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
+  const int dir = isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
   cudaEvent_t* ev = p->ev_ok ? p->ev + 4 : nullptr;
   for (int t = 0; t < p->ntransf; ++t) {
     char* ct = (char*)c + (size_t)t * (size_t)p->M * p->csize;
     char* ft = (char*)f + (size_t)t * (size_t)p->Ntot * p->csize;
-    if (p->type == 1) {
+    if (type == 1) {
       CUDA_TRY(cudaMemsetAsync(p->grid, 0, (size_t)p->ngrid * p->csize, p->stream));
       if (ev && t == 0) cudaEventRecord(ev[0], p->stream);
       if (p->M > 0) {
@@ -482,9 +495,9 @@ int nufft_execute(nufft_plan p, void* c, void* f) {
     cufftResult r = p->dbl ? cufftExecZ2Z(p->fft, (cufftDoubleComplex*)p->grid, (cufftDoubleComplex*)p->grid, dir)
                            : cufftExecC2C(p->fft, (cufftComplex*)p->grid, (cufftComplex*)p->grid, dir);
     if (r != CUFFT_SUCCESS) return NUFFT_ERR_CUFFT;
-    if (p->type == 2 && p->M > 0) CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
+    if (type == 2 && p->M > 0) CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
     if (ev && t == 0) cudaEventRecord(ev[2], p->stream);
-    if (p->type == 1) {
+    if (type == 1) {
       CUDA_TRY(launch_deconv(p->dbl, mg, p->grid, ft, p->pk[0], p->pk[1], p->pk[2], p->stream));
     } else if (p->M > 0) {
       CUDA_TRY(launch_interp(p->dbl, g, p->beta, s, p->grid, ct, p->small + 2, p->interp_cfg, p->stream));
@@ -494,6 +507,95 @@ int nufft_execute(nufft_plan p, void* c, void* f) {
   p->last_steps = 2;
   return NUFFT_OK;
 }
+
+int plan_set_stream(nufft_plan p, cudaStream_t s) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  p->stream = s;
+  if (p->fft_ok && cufftSetStream(p->fft, s) != CUFFT_SUCCESS) return NUFFT_ERR_CUFFT;
+  return NUFFT_OK;
+}
+
+int plan_reserve(nufft_plan p, int64_t mcap) {
+  if (!p || mcap < 0) return NUFFT_ERR_BAD_ARG;
+  if (mcap >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_TOO_BIG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  const Geom& g = p->g;
+  if (mcap > p->Mcap) {
+    cudaFree(p->rec);
+    p->rec = nullptr;
+    p->Mcap = 0;
+    size_t rsz = p->dbl ? sizeof(RecD) : sizeof(RecF);
+    if (dev_alloc(&p->rec, rsz * (size_t)mcap) != cudaSuccess) return NUFFT_ERR_ALLOC;
+    p->Mcap = mcap;
+  }
+  int64_t need = std::min<int64_t>(g.nbins, mcap) + mcap / g.maxsub + 1;
+  if (need > p->subcap) {
+    cudaFree(p->sub_bin);
+    cudaFree(p->sub_pt0);
+    cudaFree(p->sub_cnt);
+    p->sub_bin = p->sub_pt0 = p->sub_cnt = nullptr;
+    p->subcap = 0;
+    if (dev_alloc(&p->sub_bin, sizeof(int) * (size_t)need) != cudaSuccess ||
+        dev_alloc(&p->sub_pt0, sizeof(int) * (size_t)need) != cudaSuccess ||
+        dev_alloc(&p->sub_cnt, sizeof(int) * (size_t)need) != cudaSuccess)
+      return NUFFT_ERR_ALLOC;
+    p->subcap = need;
+  }
+  return NUFFT_OK;
+}
+
+// Device bytes a plan holds: its buffers plus cuFFT's work area.
+size_t plan_device_bytes(nufft_plan p) {
+  if (!p) return 0;
+  size_t rs = p->dbl ? 8 : 4, cs = p->csize;
+  size_t b = (size_t)p->ngrid * cs + 4 * sizeof(int) * (size_t)p->g.nbins + 4 * sizeof(int);
+  for (int i = 0; i < 3; ++i) b += (size_t)p->N[i] * rs;
+  b += (size_t)p->Mcap * (p->dbl ? sizeof(RecD) : sizeof(RecF)) + 3 * sizeof(int) * (size_t)p->subcap;
+  size_t ws = 0;
+  if (p->fft_ok && cufftGetSize(p->fft, &ws) == CUFFT_SUCCESS) b += ws;
+  return b;
+}
+
+// Upper estimate of plan_device_bytes before the plan exists (default options,
+// point capacity mcap); cuFFT's work area is bounded by one more fine grid.
+int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes) {
+  if (!bytes || !nmodes || dim < 1 || dim > 3 || mcap < 0 || (prec != NUFFT_C64 && prec != NUFFT_C128))
+    return NUFFT_ERR_BAD_ARG;
+  int w;
+  double beta;
+  int64_t n[3] = {1, 1, 1};
+  int st = choose_params_impl(dim, nmodes, eps, prec, &w, &beta, n);
+  if (st < 0) return st;
+  const bool dbl = prec == NUFFT_C128;
+  Geom g;
+  g.d = dim;
+  g.w = w;
+  g.half = w / 2;
+  for (int i = 0; i < 3; ++i) g.n[i] = (int)n[i];
+  g.maxsub = dbl ? 512 : 1024;
+  nufft_opts o;
+  nufft_default_opts(&o);
+  choose_bins(g, dbl, o);
+  size_t cs = dbl ? 16 : 8, rs = dbl ? 8 : 4;
+  size_t ngrid = (size_t)n[0] * (size_t)n[1] * (size_t)n[2];
+  size_t b = 2 * ngrid * cs + 4 * sizeof(int) * (size_t)g.nbins + 4 * sizeof(int);
+  for (int i = 0; i < dim; ++i) b += (size_t)nmodes[i] * rs;
+  int64_t subcap = std::min<int64_t>(g.nbins, mcap) + mcap / g.maxsub + 1;
+  b += (size_t)mcap * (dbl ? sizeof(RecD) : sizeof(RecF)) + 3 * sizeof(int) * (size_t)subcap;
+  *bytes = b;
+  return NUFFT_OK;
+}
+
+int plan_modes(nufft_plan p, int64_t* N, int* dim) {
+  if (!p) return NUFFT_ERR_BAD_ARG;
+  for (int i = 0; i < 3; ++i) N[i] = p->N[i];
+  *dim = p->dim;
+  return NUFFT_OK;
+}
+
+}  // namespace nufft
+
+extern "C" {
 
 int nufft_destroy(nufft_plan p) {
   if (!p) return NUFFT_OK;
