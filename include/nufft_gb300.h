@@ -69,7 +69,9 @@ typedef struct {
   int bin_size[3];    /* bin extent in fine-grid cells per dimension (0: choose from d, w, precision) */
   int max_subprob;    /* most points one thread block handles at a time (0: choose) */
   int threads;        /* threads per block of the spread / interp kernels (0: choose) */
-  int reserved[8];    /* set to zero */
+  int sparse_max;     /* subproblems of at most this many points (<= 32) run one per warp straight
+                         on the fine grid instead of through a shared-memory tile (0: 32, -1: never) */
+  int reserved[7];    /* set to zero */
 } nufft_opts;
 
 /* Fill *o with defaults.  Returns NUFFT_OK, or NUFFT_ERR_BAD_ARG for o == NULL. */

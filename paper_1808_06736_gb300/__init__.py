@@ -42,7 +42,7 @@ class NufftError(RuntimeError):
 class nufft_opts(ctypes.Structure):
     _fields_ = [("debug", ctypes.c_int), ("chkbnds", ctypes.c_int), ("modeord", ctypes.c_int),
                 ("bin_size", ctypes.c_int * 3), ("max_subprob", ctypes.c_int), ("threads", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("sparse_max", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 _lib = None

@@ -191,9 +191,21 @@ __device__ __forceinline__ int block_incl_scan(int v, int* wsum) {
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, const int* __restrict__ cnt,
+// Per bin: its full chunks of maxsub points and a remainder; the remainder is
+// a tiled subproblem when it holds more than smax points and a per-warp
+// ("sparse") one otherwise.  Tiled subproblems are numbered in bin order from
+// 0 (sub_first); the sparse ones are appended after them by k_sublist.
+__device__ __forceinline__ void split_bin(int c, int maxsub, int smax, int* ntiled, int* sparse) {
+  const int full = c / maxsub, rem = c - full * maxsub;
+  const bool sp = rem > 0 && rem <= smax;
+  *ntiled = full + ((rem > 0 && !sp) ? 1 : 0);
+  *sparse = sp ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, int smax, const int* __restrict__ cnt,
                                                int* __restrict__ start, int* __restrict__ cursor,
-                                               int* __restrict__ sub_first, int* __restrict__ nsub) {
+                                               int* __restrict__ sub_first, int* __restrict__ nsub,
+                                               int* __restrict__ nsparse) {
   __shared__ int wsum[32];
   __shared__ int carry[2];
   if (threadIdx.x == 0) carry[0] = carry[1] = 0;
@@ -201,7 +213,8 @@ __global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, const int*
   for (int base = 0; base < nbins; base += blockDim.x) {
     const int b = base + threadIdx.x;
     const int c = b < nbins ? cnt[b] : 0;
-    const int sc = (c + maxsub - 1) / maxsub;
+    int sc, sp;
+    split_bin(c, maxsub, smax, &sc, &sp);
     const int cp = carry[0], cs = carry[1];
     const int ip = block_incl_scan(c, wsum);
     const int is = block_incl_scan(sc, wsum);
@@ -216,20 +229,44 @@ __global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, const int*
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *nsub = carry[1];
+  if (threadIdx.x == 0) {
+    *nsub = carry[1];
+    *nsparse = 0;
+  }
 }
 
-__global__ void k_sublist(int nbins, int maxsub, const int* __restrict__ cnt,
+// Tiled subproblems at sub_first[b] + k; a sparse remainder at nsub + (an
+// append position, taken once per warp so neighbouring bins stay close).
+__global__ void k_sublist(int nbins, int maxsub, int smax, const int* __restrict__ cnt,
                           const int* __restrict__ start, const int* __restrict__ sub_first,
-                          int* __restrict__ sub_bin, int* __restrict__ sub_pt0,
-                          int* __restrict__ sub_cnt) {
+                          const int* __restrict__ nsub, int* __restrict__ nsparse, int* __restrict__ sub_bin,
+                          int* __restrict__ sub_pt0, int* __restrict__ sub_cnt) {
+  const int nt = *nsub;
+  const int lane = threadIdx.x & 31;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
-    int c = cnt[b];
-    int s0 = sub_first[b], p0 = start[b];
-    for (int k = 0; k * maxsub < c; ++k) {
+    const int c = cnt[b];
+    int ntl, sp;
+    split_bin(c, maxsub, smax, &ntl, &sp);
+    const int s0 = sub_first[b], p0 = start[b];
+    for (int k = 0; k < ntl; ++k) {
       sub_bin[s0 + k] = b;
       sub_pt0[s0 + k] = p0 + k * maxsub;
       sub_cnt[s0 + k] = min(maxsub, c - k * maxsub);
+    }
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, sp);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(nsparse, __popc(m));
+      base = __shfl_sync(act, base, leader);
+      if (sp) {
+        const int q = nt + base + __popc(m & ((1u << lane) - 1u));
+        const int full = c / maxsub;
+        sub_bin[q] = b;
+        sub_pt0[q] = p0 + full * maxsub;
+        sub_cnt[q] = c - full * maxsub;
+      }
     }
   }
 }
@@ -336,7 +373,8 @@ template <typename T>
 cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, const void* y,
                      const void* z, int chk, int* bin_count, int* bin_start, int* sub_first,
                      int* cursor, void* rec, int* sub_bin, int* sub_pt0, int* sub_cnt, int* nsub,
-                     int* err, cudaStream_t st, cudaEvent_t* ev, const BatchTable& bt, int nbins) {
+                     int* nsparse, int* err, cudaStream_t st, cudaEvent_t* ev, const BatchTable& bt,
+                     int nbins) {
   const T* xp = (const T*)x;
   const T* yp = g.d > 1 ? (const T*)y : xp;
   const T* zp = g.d > 2 ? (const T*)z : xp;
@@ -348,10 +386,11 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
-  k_scan<<<1, 1024, 0, st>>>(nbins, g.maxsub, bin_count, bin_start, cursor, sub_first, nsub);
+  const int smax = g.sparse_max < g.maxsub ? g.sparse_max : g.maxsub - 1;
+  k_scan<<<1, 1024, 0, st>>>(nbins, g.maxsub, smax, bin_count, bin_start, cursor, sub_first, nsub, nsparse);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sublist<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, g.maxsub, bin_count, bin_start,
-                                                   sub_first, sub_bin, sub_pt0, sub_cnt);
+  k_sublist<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, g.maxsub, smax, bin_count, bin_start, sub_first, nsub,
+                                                   nsparse, sub_bin, sub_pt0, sub_cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], st);
   if (M > 0) {
@@ -368,14 +407,14 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
 cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
                           int* sub_first, int* cursor, void* rec, int* sub_bin,
-                          int* sub_pt0, int* sub_cnt, int* nsub, int* err, cudaStream_t st,
+                          int* sub_pt0, int* sub_cnt, int* nsub, int* nsparse, int* err, cudaStream_t st,
                           cudaEvent_t* ev, const BatchTable& bt, int nbins) {
   if (nbins <= 0) nbins = g.nbins;
   if (dbl)
     return setpts_t<double>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
-                            rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev, bt, nbins);
+                            rec, sub_bin, sub_pt0, sub_cnt, nsub, nsparse, err, st, ev, bt, nbins);
   return setpts_t<float>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
-                         rec, sub_bin, sub_pt0, sub_cnt, nsub, err, st, ev, bt, nbins);
+                         rec, sub_bin, sub_pt0, sub_cnt, nsub, nsparse, err, st, ev, bt, nbins);
 }
 
 }  // namespace nufft

@@ -80,6 +80,7 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
   g.w = w;
   g.half = w / 2;
   g.maxsub = kMaxSub;
+  g.sparse_max = 32;
   int64_t ngrid = 1;
   for (int i = 0; i < 3; ++i) {
     int64_t v = i < dim ? n[i] : 1;
@@ -112,7 +113,7 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
   int* bin_start = (int*)(s + o_start);
   int* sub_first = (int*)(s + o_first);
   int* cursor = (int*)(s + o_cursor);
-  int* small = (int*)(s + o_small);  // [0] error word, [1] nsub, [2] work counter
+  int* small = (int*)(s + o_small);  // [0] error word, [1] tiled / [3] sparse subproblems, [2] work counter
   int* sub_bin = (int*)(s + o_subbin);
   int* sub_pt0 = (int*)(s + o_subpt0);
   int* sub_cnt = (int*)(s + o_subcnt);
@@ -124,12 +125,12 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
   if (cudaMemsetAsync(grid, 0, (size_t)ngrid * 8, st_) != cudaSuccess) return NUFFT_ERR_CUDA;
   FoldConst fc = make_fold_const(g);
   if (launch_setpts(false, g, fc, M, x, y, z, 0, bin_count, bin_start, sub_first, cursor, rec, sub_bin,
-                    sub_pt0, sub_cnt, small + 1, small + 0, st_, nullptr) != cudaSuccess)
+                    sub_pt0, sub_cnt, small + 1, small + 3, small + 0, st_, nullptr) != cudaSuccess)
     return NUFFT_ERR_CUDA;
   if (M == 0) return NUFFT_OK;
   LaunchCfg cfg;
   if (spread_config(false, g, 256, &cfg) != cudaSuccess) return NUFFT_ERR_CUDA;
-  Sorted so{rec, sub_bin, sub_pt0, sub_cnt, small + 1};
+  Sorted so{rec, sub_bin, sub_pt0, sub_cnt, small + 1, small + 3};
   if (launch_spread(false, g, beta, so, c, grid, small + 2, cfg, st_) != cudaSuccess) return NUFFT_ERR_CUDA;
   return NUFFT_OK;
 }

@@ -27,6 +27,7 @@ struct Geom {
   int nbins;     // bin ids in use: ns[0] ns[1] ns[2] sb[0] sb[1] sb[2] (ids of padding bins stay empty)
   int ntile;     // T[0] T[1] T[2]
   int maxsub;    // most points in one subproblem
+  int sparse_max;  // subproblems with at most this many points take the per-warp path (0: none)
 };
 
 // Bin ids run over super-blocks of sb[0] x sb[1] x sb[2] bins, dimension 1
@@ -134,7 +135,8 @@ struct Sorted {
   const int* sub_bin;  // [nsub] bin of each subproblem
   const int* sub_pt0;  // [nsub] first record of each subproblem
   const int* sub_cnt;  // [nsub] number of records
-  const int* nsub;     // device scalar
+  const int* nsub;     // device scalar: tiled subproblems, list entries [0, nsub)
+  const int* nsparse;  // device scalar: per-warp subproblems, entries [nsub, nsub + nsparse)
 };
 
 // --- setpts (binsort.cu) ------------------------------------------------------
@@ -149,7 +151,7 @@ FoldConst make_fold_const(const Geom& g);
 cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
                           int* sub_first, int* cursor, void* rec, int* sub_bin, int* sub_pt0,
-                          int* sub_cnt, int* nsub, int* err, cudaStream_t st,
+                          int* sub_cnt, int* nsub, int* nsparse, int* err, cudaStream_t st,
                           cudaEvent_t* ev /* 4 events or nullptr */,
                           const BatchTable& bt = BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0},
                           int nbins = 0 /* bin ids over all transforms; 0: g.nbins */);

@@ -40,7 +40,7 @@ struct nufft_plan_s {
   int* bin_start = nullptr;
   int* sub_first = nullptr;
   int* cursor = nullptr;  // per-bin scatter cursors
-  int* small = nullptr;  // [0] error word, [1] nsub, [2] work counter
+  int* small = nullptr;  // [0] error word, [1] tiled subproblems, [2] work counter, [3] sparse subproblems
   int64_t M = -1;
   int64_t Mcap = 0;
   void* rec = nullptr;
@@ -205,6 +205,12 @@ void choose_bins(Geom& g, bool dbl, const nufft_opts& o) {
   }
 }
 
+// subproblems of at most this many points take the per-warp path (0: none)
+int sparse_max_of(const nufft_opts& o) {
+  if (o.sparse_max < 0) return 0;
+  return o.sparse_max == 0 ? 32 : std::min(o.sparse_max, 32);
+}
+
 int fail(nufft_plan p, int code) {
   nufft_destroy(p);
   return code;
@@ -364,6 +370,7 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   g.half = w / 2;
   for (int i = 0; i < 3; ++i) g.n[i] = (int)n[i];
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
+  g.sparse_max = sparse_max_of(p->opts);
   choose_bins(g, p->dbl, p->opts);
   int threads = p->opts.threads > 0 ? p->opts.threads : 256;
   if (threads % 32 != 0 || threads > 256) return fail(p, NUFFT_ERR_BAD_ARG);
@@ -444,7 +451,7 @@ int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const vo
   FoldConst fc = make_fold_const(g);
   cudaError_t e = launch_setpts(p->dbl, g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
                                 p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0,
-                                p->sub_cnt, p->small + 1, p->small + 0, p->stream,
+                                p->sub_cnt, p->small + 1, p->small + 3, p->small + 0, p->stream,
                                 p->ev_ok ? p->ev : nullptr);
   if (e != cudaSuccess) return NUFFT_ERR_CUDA;
   p->M = M;
@@ -467,7 +474,7 @@ int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f) {
   if (!f || (p->M > 0 && !c)) return NUFFT_ERR_BAD_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
   const Geom& g = p->g;
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1};
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
   ModeGeom mg;
   mg.d = p->dim;
   mg.modeord = p->opts.modeord ? 1 : 0;
@@ -573,6 +580,7 @@ int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, in
   g.half = w / 2;
   for (int i = 0; i < 3; ++i) g.n[i] = (int)n[i];
   g.maxsub = dbl ? 512 : 1024;
+  g.sparse_max = 32;
   nufft_opts o;
   nufft_default_opts(&o);
   choose_bins(g, dbl, o);
@@ -703,7 +711,7 @@ struct nufft_batch_s {
   int* bin_start = nullptr;
   int* sub_first = nullptr;
   int* cursor = nullptr;
-  int* small = nullptr;  // [0] error word, [1] nsub, [2] work counter
+  int* small = nullptr;  // [0] error word, [1] tiled subproblems, [2] work counter, [3] sparse subproblems
   int64_t M = -1, Mcap = 0, subcap = 0;
   void* rec = nullptr;
   int* sub_bin = nullptr;
@@ -731,7 +739,7 @@ int batch_fail(nufft_batch p, int code) {
 // The execute sequence, enqueued on the plan's stream.
 int batch_enqueue(nufft_batch p, void* c, void* f) {
   const BatchTable bt = table_of(p);
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1};
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
   const int dir = p->isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
   const int modeord = p->opts.modeord ? 1 : 0;
   auto ffts = [&]() -> int {
@@ -807,6 +815,7 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   g.w = p->w;
   g.half = p->w / 2;
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
+  g.sparse_max = sparse_max_of(p->opts);
   for (int i = 0; i < 3; ++i) {
     int64_t mx = 1;
     for (int t = 0; t < B; ++t) mx = std::max(mx, n[(size_t)t * 3 + i]);
@@ -973,7 +982,7 @@ int nufft_batch_setpts(nufft_batch p, const int64_t* offsets, const void* x, con
   FoldConst fc = make_fold_const(p->g);
   cudaError_t e = launch_setpts(p->dbl, p->g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
                                 p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1,
-                                p->small + 0, p->stream, nullptr, table_of(p), p->total_bins);
+                                p->small + 3, p->small + 0, p->stream, nullptr, table_of(p), p->total_bins);
   if (e != cudaSuccess) return NUFFT_ERR_CUDA;
   p->M = M;
   return NUFFT_OK;

@@ -569,6 +569,229 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T k
   }
 }
 
+// ------------------------------------------------- sparse subproblems
+// Subproblems of at most 32 points (low point density: most bins hold a few
+// points or none) skip the shared-memory tile, whose zeroing, flushing or
+// loading would cost far more than their w^d contributions per point.  One
+// warp takes one such subproblem: lane j holds point j; per pass the warp
+// handles PP = max(1, 32 / w^d) points, its lanes computing the per-dimension
+// ES weights into a small per-warp buffer, then each lane owns one stencil
+// cell of one point (lanes along x first, so a warp's accesses fall in
+// contiguous rows of the fine grid) and adds to / gathers from the fine grid
+// directly, wrapping periodically.
+template <int W, int D>
+struct Sparse {
+  static constexpr int CP = (D == 1) ? W : (D == 2 ? W * W : W * W * W);  // cells per point
+  static constexpr int PP = CP >= 32 ? 1 : 32 / CP;                      // points per pass
+  static constexpr int NW = PP * W * D;                                  // weights per pass (<= 48)
+  static constexpr int WB = 64;                                          // weight buffer per warp
+};
+
+// The subproblem's geometry for a batch: its transform's grid, bin id and offset.
+__device__ __forceinline__ void sparse_geometry(const Geom& g, const BatchTable& bt, int& bin, Geom& gg,
+                                                long long& goff) {
+  gg = g;
+  goff = 0;
+  if (bt.B > 0) {
+    const int t = batch_find(bt.boff, bt.B, bin);
+    const BatchGeom tg = bt.bg[t];
+    batch_apply(gg, tg);
+    bin -= tg.boff;
+    goff = tg.goff;
+  }
+}
+
+// Weights of the points jb .. jb+PP-1 (records held by lanes jb + p) into wb,
+// entry p*W*D + d*W + t.  Every lane takes part in the shuffles.
+template <typename T, int D, int W>
+__device__ __forceinline__ void sparse_weights(const typename Traits<T>::Rec& r, int jb, const Geom& gg, T kpar,
+                                               T* wb) {
+  using S = Sparse<W, D>;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int e0 = 0; e0 < S::NW; e0 += 32) {
+    const int e = e0 + lane;
+    const int p = e / (W * D), dd = (e / W) % D, t = e % W;
+    const int src = (jb + p) & 31;
+    const T v0 = __shfl_sync(0xffffffffu, r.v[0], src);
+    const T v1 = __shfl_sync(0xffffffffu, r.v[1], src);
+    const T v2 = __shfl_sync(0xffffffffu, r.v[2], src);
+    if (e < S::NW) {
+      const T v = dd == 0 ? v0 : (dd == 1 ? v1 : v2);
+      const int il = min((int)v, gg.B[dd] - 1);
+      const T f = v - T(il);
+      wb[e] = es_eval(node_z<W>(t, stencil_step<W>(f), f), kpar);
+    }
+  }
+  __syncwarp();
+}
+
+// Fine-grid index of stencil cell `cell` of the point whose record is v, and
+// the cell's weight from wb (point slot p).
+template <typename T, int D, int W>
+__device__ __forceinline__ long long sparse_cell(const T* v, const int* org, const Geom& gg, const T* wb, int p,
+                                                 int cell, T& wt) {
+  const int i0 = cell % W, i1 = (cell / W) % W, i2 = cell / (W * W);
+  const int ii[3] = {i0, i1, i2};
+  long long idx = 0, stride = 1;
+  wt = T(1);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int il = min((int)v[d], gg.B[d] - 1);
+    const int a = org[d] + il + stencil_step<W>(v[d] - T(il));
+    idx += (long long)wrap_idx(a + ii[d], gg.n[d]) * stride;
+    stride *= gg.n[d];
+    wt *= wb[p * W * D + d * W + ii[d]];
+  }
+  return idx;
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_spread_sparse(Geom g, T kpar, Sorted s,
+                                                       const typename Traits<T>::C* __restrict__ c,
+                                                       typename Traits<T>::C* __restrict__ grid, BatchTable bt) {
+  using C = typename Traits<T>::C;
+  using Rec = typename Traits<T>::Rec;
+  using S = Sparse<W, D>;
+  __shared__ T wbuf[8][S::WB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nt = *s.nsub, nsp = *s.nsparse;
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(s.rec);
+  T* wb = wbuf[wid];
+  for (int i = blockIdx.x * 8 + wid; i < nsp; i += gridDim.x * 8) {
+    const int sub = nt + i;
+    int bin = s.sub_bin[sub];
+    const int p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+    Geom gg;
+    long long goff;
+    sparse_geometry(g, bt, bin, gg, goff);
+    int org[3];
+    tile_origin(gg, bin, org);
+    Rec r;
+    r.v[0] = r.v[1] = r.v[2] = T(0);
+    C cv;
+    cv.x = cv.y = T(0);
+    if (lane < cnt) {
+      r = rec[p0 + lane];
+      cv = load_once(c + r.idx);
+    }
+    C* gt = grid + goff;
+    for (int jb = 0; jb < cnt; jb += S::PP) {
+      sparse_weights<T, D, W>(r, jb, gg, kpar, wb);
+      if (S::PP > 1) {
+        const int p = lane / S::CP, cell = lane - p * S::CP;
+        const int src = (jb + p) & 31;
+        T v[3];
+        v[0] = __shfl_sync(0xffffffffu, r.v[0], src);
+        v[1] = __shfl_sync(0xffffffffu, r.v[1], src);
+        v[2] = __shfl_sync(0xffffffffu, r.v[2], src);
+        const T cx = __shfl_sync(0xffffffffu, cv.x, src), cy = __shfl_sync(0xffffffffu, cv.y, src);
+        if (p < S::PP && jb + p < cnt) {
+          T wt;
+          const long long q = sparse_cell<T, D, W>(v, org, gg, wb, p, cell, wt);
+          red_add(gt + q, cx * wt, cy * wt);
+        }
+      } else {
+        const T v[3] = {__shfl_sync(0xffffffffu, r.v[0], jb), __shfl_sync(0xffffffffu, r.v[1], jb),
+                        __shfl_sync(0xffffffffu, r.v[2], jb)};
+        const T cx = __shfl_sync(0xffffffffu, cv.x, jb), cy = __shfl_sync(0xffffffffu, cv.y, jb);
+        for (int cell = lane; cell < S::CP; cell += 32) {
+          T wt;
+          const long long q = sparse_cell<T, D, W>(v, org, gg, wb, 0, cell, wt);
+          red_add(gt + q, cx * wt, cy * wt);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) k_interp_sparse(Geom g, T kpar, Sorted s,
+                                                       const typename Traits<T>::C* __restrict__ grid,
+                                                       typename Traits<T>::C* __restrict__ c, BatchTable bt) {
+  using C = typename Traits<T>::C;
+  using Rec = typename Traits<T>::Rec;
+  using S = Sparse<W, D>;
+  __shared__ T wbuf[8][S::WB];
+  __shared__ C part[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nt = *s.nsub, nsp = *s.nsparse;
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(s.rec);
+  T* wb = wbuf[wid];
+  for (int i = blockIdx.x * 8 + wid; i < nsp; i += gridDim.x * 8) {
+    const int sub = nt + i;
+    int bin = s.sub_bin[sub];
+    const int p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+    Geom gg;
+    long long goff;
+    sparse_geometry(g, bt, bin, gg, goff);
+    int org[3];
+    tile_origin(gg, bin, org);
+    Rec r;
+    r.v[0] = r.v[1] = r.v[2] = T(0);
+    r.idx = 0;
+    if (lane < cnt) r = rec[p0 + lane];
+    const C* gt = grid + goff;
+    for (int jb = 0; jb < cnt; jb += S::PP) {
+      sparse_weights<T, D, W>(r, jb, gg, kpar, wb);
+      if (S::PP > 1) {
+        const int p = lane / S::CP, cell = lane - p * S::CP;
+        const int src = (jb + p) & 31;
+        T v[3];
+        v[0] = __shfl_sync(0xffffffffu, r.v[0], src);
+        v[1] = __shfl_sync(0xffffffffu, r.v[1], src);
+        v[2] = __shfl_sync(0xffffffffu, r.v[2], src);
+        C acc;
+        acc.x = acc.y = T(0);
+        if (p < S::PP && jb + p < cnt) {
+          T wt;
+          const long long q = sparse_cell<T, D, W>(v, org, gg, wb, p, cell, wt);
+          const C gv = __ldg(gt + q);
+          acc.x = gv.x * wt;
+          acc.y = gv.y * wt;
+        }
+        part[wid][lane] = acc;
+        const int dst = __shfl_sync(0xffffffffu, r.idx, (jb + lane) & 31);
+        __syncwarp();
+        if (lane < S::PP && jb + lane < cnt) {
+          C sum;
+          sum.x = sum.y = T(0);
+          for (int k = 0; k < S::CP; ++k) {
+            sum.x += part[wid][lane * S::CP + k].x;
+            sum.y += part[wid][lane * S::CP + k].y;
+          }
+          store_once(c + dst, sum);
+        }
+      } else {
+        const T v[3] = {__shfl_sync(0xffffffffu, r.v[0], jb), __shfl_sync(0xffffffffu, r.v[1], jb),
+                        __shfl_sync(0xffffffffu, r.v[2], jb)};
+        T sr = T(0), si = T(0);
+        for (int cell = lane; cell < S::CP; cell += 32) {
+          T wt;
+          const long long q = sparse_cell<T, D, W>(v, org, gg, wb, 0, cell, wt);
+          const C gv = __ldg(gt + q);
+          sr = fma(gv.x, wt, sr);
+          si = fma(gv.y, wt, si);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        const int dst = __shfl_sync(0xffffffffu, r.idx, jb);
+        if (lane == 0) {
+          C out;
+          out.x = sr;
+          out.y = si;
+          store_once(c + dst, out);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // shared-memory bytes of each kernel
 template <typename T, int D>
 inline size_t spread_bytes(const Geom& g) {
@@ -609,6 +832,11 @@ cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* 
   kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
       g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
       reinterpret_cast<typename Traits<T>::C*>(grid), work, bt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.sparse_max <= 0) return e;
+  k_spread_sparse<T, D, W><<<2 * cfg.blocks, 256, 0, st>>>(
+      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
+      reinterpret_cast<typename Traits<T>::C*>(grid), bt);
   return cudaGetLastError();
 }
 
@@ -629,6 +857,11 @@ cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* 
   kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
       g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
       reinterpret_cast<typename Traits<T>::C*>(c), work, bt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.sparse_max <= 0) return e;
+  k_interp_sparse<T, D, W><<<2 * cfg.blocks, 256, 0, st>>>(
+      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
+      reinterpret_cast<typename Traits<T>::C*>(c), bt);
   return cudaGetLastError();
 }
 

@@ -220,3 +220,32 @@ def test_spread_widths_3d_c64(pkg, oracle_mod, eps, kind):
     # below eps = 1e-5 complex64 is held to its rounding floor (Remark r:rounding), not to 10 eps
     bar = max(10 * eps, 2e-5)
     assert oracle_mod.rel_l2(g[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= bar
+
+
+SPARSE_SIZES = {1: ([5000], 150), 2: ([200, 150], 2000), 3: ([40, 36, 30], 5000)}
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex64, 1e-3), (np.complex128, 1e-9)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_sparse_subproblems(pkg, oracle_mod, cdtype, eps, d, kind):
+    """Low point density (a few points per bin): subproblems of <= 32 points take the
+    per-warp path straight on the fine grid.  Uniform points make nearly all of them
+    sparse; clustered points mix both paths in one launch.  Against the exact sums
+    (10 eps) and against the tiled-only path (sparse_max = -1; rounding budget), also
+    with a threshold of 8 points."""
+    Ns, M = SPARSE_SIZES[d]
+    xs, c, f = case_inputs(d, Ns, M, kind, cdtype, seed=3000 + 10 * d)
+    x64 = [v.astype(np.float64) for v in xs]
+    o1_1 = oracle_mod.direct_type1(x64, c, 1, Ns)
+    o1_2 = oracle_mod.direct_type2(x64, f, -1, Ns)
+    bar = 10 * max(eps, 2e-6 if cdtype == np.complex64 else 0)
+    ref1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, sparse_max=-1)
+    ref2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, sparse_max=-1)
+    for smax in (0, 8):
+        g1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, sparse_max=smax)
+        g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, sparse_max=smax)
+        assert oracle_mod.rel_l2(g1[0], o1_1) <= bar
+        assert oracle_mod.rel_l2(g2[0], o1_2) <= bar
+        assert oracle_mod.rel_l2(g1[0], ref1[0]) <= TOL_SAME[cdtype]
+        assert oracle_mod.rel_l2(g2[0], ref2[0]) <= TOL_SAME[cdtype]

@@ -264,13 +264,14 @@ def test_budget_eviction_and_rejection(pkg):
     import torch
     p, S = pkg
     dev = torch.device("cuda:0")
-    # admission counts about two fine grids per entry (grid + cuFFT's work area):
-    # 268 MB, 201 MB, 113 MB, then 128 MB needs the least recently used entry evicted
-    budget = 600 << 20
+    # admission estimates two fine grids per new entry (grid + a bound on cuFFT's work
+    # area, 220..268 MB here) and counts at least one grid (110..134 MB) per resident
+    # entry, so no more than two entries fit and the five shapes force evictions
+    budget = 400 << 20
     srv = S.Server(budget_bytes=budget, max_inflight=4)
     xs = I.torch_points(111, 20_000, 3, "uniform", dev, torch.float32)
     c = I.torch_complex_normal(112, 20_000, dev, torch.complex64)
-    shapes = [(128, 128, 128), (128, 128, 96), (96, 96, 96), (100, 100, 100), (96, 96, 96)]
+    shapes = [(128, 128, 128), (128, 128, 120), (120, 120, 120), (128, 120, 120), (128, 128, 128)]
     for i, n in enumerate(shapes):
         srv.type1(xs, c, n, eps=1e-5, tag=i)
     got = _collect(srv, len(shapes))
