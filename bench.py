@@ -484,6 +484,8 @@ def run_serving(args):
     (a) the request loop (Server: --slots slots, resident plan entries) and
     (b) the plain path: one request at a time through cached Plans (gradient
     requests through the autograd functions), synchronising after each.
+    Both arms take gradient requests' point gradient through the ES kernel's
+    derivative (xgrad="kernel").
     Open loop: each request is submitted at its arrival time; latency = device
     completion - arrival.  Burst: the whole trace submitted at once; points/s =
     sum of M / makespan.  Inputs are slices of pools resident in HBM; each arm
@@ -520,7 +522,7 @@ def run_serving(args):
             return srv.type1(xs, c, q["modes"], eps=q["eps"], isign=q["isign"], tag=tag)
         if q["kind"] == 2:
             return srv.type2(xs, f, eps=q["eps"], isign=q["isign"], tag=tag)
-        return srv.lsq_grad(xs, f, y, eps=q["eps"], isign=q["isign"], tag=tag)
+        return srv.lsq_grad(xs, f, y, eps=q["eps"], isign=q["isign"], tag=tag, xgrad="kernel")
 
     def collect(srv, n, got):
         t_end = time.time() + 600
@@ -574,7 +576,7 @@ def run_serving(args):
         else:
             xg = torch.stack(xs).requires_grad_()
             fg = f.detach().clone().requires_grad_()
-            cc = AG.nufft_type2(xg, fg, eps=q["eps"], isign=q["isign"], cache=cache)
+            cc = AG.nufft_type2(xg, fg, eps=q["eps"], isign=q["isign"], cache=cache, xgrad="kernel")
             loss = ((cc - y).abs() ** 2).sum()
             loss.backward()
         torch.cuda.synchronize()
@@ -607,7 +609,8 @@ def run_serving(args):
                   "burst_pts_per_s": total_pts / mk_plain, "burst_makespan_s": mk_plain,
                   "path": "cached Plan per request shape, one request at a time, synchronised"},
         "burst_throughput_vs_plain": mk_plain / mk_served,
-        "points": "each request counts its M points once (a gradient request runs 2 + d transforms on them)",
+        "points": "each request counts its M points once (a gradient request runs a type-2 transform with the "
+                  "point gradient through the ES kernel's derivative and one type-1 transform on them)",
     }
 
 

@@ -124,6 +124,22 @@ int nufft_setpts(nufft_plan plan, int64_t M, const void* x, const void* y, const
  */
 int nufft_execute(nufft_plan plan, void* c, void* f);
 
+/*
+ * Type-2 plans only: nufft_execute plus the gradient of each value in its
+ * point.  Writes c as nufft_execute does and dc, dim * M complex values per
+ * transform (row d at dc + d * M holds dc_j / dx_{j,d}), obtained by
+ * differentiating the interpolation (Eq. (interp)) with the derivative of the
+ * ES kernel, phi'(z) = -beta z / sqrt(1 - z^2) phi(z) (the paper's remark on
+ * kernel derivatives, Sec. 7, notes that phi' is unbounded at z = +-1; the
+ * factor 1 / sqrt(1 - z^2) is capped at 1e3).  The exact gradient is
+ * sum_k f_k (i isign k_d) exp(i isign k.x_j); this one approximates it with a
+ * relative error a few times eps (aliased frequencies near the fine-grid size
+ * are weighted by their own size).  Transform t reads f + t N, writes
+ * c + t M and dc + t dim M.  Errors: BAD_ARG (type-1 plan, NULL pointer),
+ * NOT_SET, CUDA, CUFFT.
+ */
+int nufft_execute_grad(nufft_plan plan, void* c, void* dc, const void* f);
+
 /* Free every resource of the plan (synchronises its stream).  NULL is accepted. */
 int nufft_destroy(nufft_plan plan);
 

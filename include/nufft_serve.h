@@ -43,8 +43,13 @@ extern "C" {
 #define NUFFT_REQ_TYPE2 2    /* c = F2(x) f   (Eq. (2)) */
 #define NUFFT_REQ_LSQ_GRAD 3 /* loss = sum_j |F2(f; x)_j - y_j|^2 and its gradients in f and x */
 
+/* request flags */
+#define NUFFT_FLAG_XGRAD_KERNEL 1 /* LSQ_GRAD: grad_x through the ES kernel's derivative (nufft_execute_grad,
+                                     one FFT) instead of dim extra type-2 transforms of (i k_d) f */
+
 typedef struct {
   int kind;            /* NUFFT_REQ_* */
+  int flags;           /* NUFFT_FLAG_* or 0 */
   int dim;             /* 1, 2 or 3 */
   int64_t nmodes[3];   /* N_1 .. N_dim (entries above dim ignored) */
   int isign;           /* +1 or -1: the sign of the exponent (of F2 for LSQ_GRAD) */

@@ -17,7 +17,7 @@ from . import build as _build
 
 __all__ = [
     "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
-    "nufft_execute", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
+    "nufft_execute", "nufft_execute_grad", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
     "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235",
     "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
     "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy",
@@ -68,6 +68,7 @@ def _L():
                                    ctypes.POINTER(vp)]
     lib.nufft_setpts.argtypes = [vp, i64, vp, vp, vp]
     lib.nufft_execute.argtypes = [vp, vp, vp]
+    lib.nufft_execute_grad.argtypes = [vp, vp, vp, vp]
     lib.nufft_destroy.argtypes = [vp]
     lib.nufft_get_status.argtypes = [vp]
     lib.nufft_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
@@ -113,6 +114,10 @@ def nufft_setpts(plan, M: int, x: int, y: int, z: int) -> int:
 
 def nufft_execute(plan, c: int, f: int) -> int:
     return _L().nufft_execute(plan, ctypes.c_void_p(c or 0), ctypes.c_void_p(f or 0))
+
+
+def nufft_execute_grad(plan, c: int, dc: int, f: int) -> int:
+    return _L().nufft_execute_grad(plan, ctypes.c_void_p(c or 0), ctypes.c_void_p(dc or 0), ctypes.c_void_p(f or 0))
 
 
 def nufft_destroy(plan) -> int:
@@ -304,6 +309,34 @@ class Plan:
         if host:
             return res.to("cpu")
         return res
+
+    def execute_grad(self, f, out=None, dout=None):
+        """Type-2 plans: (c, dc) with c of shape (ntransf, M) and dc of shape
+        (ntransf, dim, M), dc[t, d, j] = d c[t, j] / d x_{j,d} through the
+        derivative of the ES kernel."""
+        torch = self._torch
+        if self.type != 2:
+            raise ValueError("execute_grad needs a type-2 plan")
+        if self.M is None:
+            raise NufftError(-6, "Plan.execute_grad")
+        d = torch.as_tensor(f).to(device=self.device, dtype=self.dtype, non_blocking=True).contiguous()
+        Nt = 1
+        for v in self.n_modes:
+            Nt *= v
+        if d.numel() != self.n_trans * Nt:
+            raise ValueError("expected %d coefficients" % (self.n_trans * Nt))
+        res = out if out is not None else torch.empty((self.n_trans, self.M), dtype=self.dtype, device=self.device)
+        dres = dout if dout is not None else torch.empty((self.n_trans, self.dim, self.M), dtype=self.dtype,
+                                                         device=self.device)
+        for t in (res, dres):
+            if not t.is_contiguous() or t.device != self.device or t.dtype != self.dtype:
+                raise ValueError("outputs must be contiguous %s tensors on %s" % (self.dtype, self.device))
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft_execute_grad(self._h, res.data_ptr(), dres.data_ptr(), d.data_ptr())
+        if st < 0:
+            raise NufftError(st, "nufft_execute_grad")
+        self._keep_exec = (d,)
+        return res, dres
 
     def status(self) -> int:
         return nufft_get_status(self._h)

@@ -10,11 +10,19 @@ tensors):
   type 2:  grad_f = F1_{-s}(x) G
            grad_x_d = Re( conj(G) * F2_s(x) [(s i k_d) f] )
 
-so every gradient is again a type-1 or type-2 transform on the GPU (d extra
-type-2 transforms for the point gradient, of the mode data multiplied by
-i k_d; the derivative of the exponential sum is exact, the only error is the
-transforms' own eps).  Plans are cached per (type, modes, eps, sign, dtype,
-device); points are set on every call.
+so every gradient is again a type-1 or type-2 transform on the GPU.  The point
+gradient has two routes (``xgrad``):
+
+  "exact"   d extra type-2 transforms of the mode data multiplied by (+-i k_d):
+            the derivative of the exponential sum, to the transforms' own eps;
+  "kernel"  one interpolation pass that also differentiates the ES kernel
+            (nufft_execute_grad, phi'(z) = -beta z / sqrt(1 - z^2) phi(z)): the
+            derivative of the type-2 approximation, whose relative error is a
+            few times eps (aliased frequencies are weighted by their own size),
+            for one FFT instead of d + 1.
+
+Plans are cached per (type, modes, eps, sign, dtype, device); points are set
+on every call.
 """
 from __future__ import annotations
 
@@ -62,24 +70,30 @@ def _ik(n_modes, d, sign, dtype, device):
 
 class _Type1(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, c, n_modes, eps, isign, cache):
+    def forward(ctx, x, c, n_modes, eps, isign, cache, xgrad):
         cdt = _complex_of(x.dtype)
         p = cache.get(1, n_modes, eps, isign, cdt, x.device)
         p.setpts(*x.unbind(0))
         f = p.execute(c).reshape(tuple(reversed(n_modes)))
         ctx.save_for_backward(x, c)
-        ctx.cfg = (n_modes, eps, isign, cache)
+        ctx.cfg = (n_modes, eps, isign, cache, xgrad)
         return f
 
     @staticmethod
     def backward(ctx, G):
         x, c = ctx.saved_tensors
-        n_modes, eps, isign, cache = ctx.cfg
+        n_modes, eps, isign, cache, xgrad = ctx.cfg
         cdt = _complex_of(x.dtype)
         p2 = cache.get(2, n_modes, eps, -isign, cdt, x.device)
         p2.setpts(*x.unbind(0))
         G = G.contiguous()
         grad_x = grad_c = None
+        if ctx.needs_input_grad[0] and xgrad == "kernel":
+            gc, dg = p2.execute_grad(G)
+            if ctx.needs_input_grad[1]:
+                grad_c = gc.reshape(c.shape)
+            grad_x = (c.unsqueeze(0) * dg[0].conj()).real
+            return grad_x, grad_c, None, None, None, None, None
         if ctx.needs_input_grad[1]:
             grad_c = p2.execute(G).reshape(c.shape)
         if ctx.needs_input_grad[0]:
@@ -88,25 +102,30 @@ class _Type1(torch.autograd.Function):
                 gd = p2.execute(G * _ik(n_modes, d, -isign, cdt, x.device)).reshape(c.shape)
                 rows.append((c * gd.conj()).real)
             grad_x = torch.stack(rows)
-        return grad_x, grad_c, None, None, None, None
+        return grad_x, grad_c, None, None, None, None, None
 
 
 class _Type2(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, f, eps, isign, cache):
+    def forward(ctx, x, f, eps, isign, cache, xgrad):
         cdt = _complex_of(x.dtype)
         n_modes = tuple(reversed(f.shape))
         p = cache.get(2, n_modes, eps, isign, cdt, x.device)
         p.setpts(*x.unbind(0))
-        c = p.execute(f).reshape(x.shape[1])
-        ctx.save_for_backward(x, f)
-        ctx.cfg = (n_modes, eps, isign, cache)
+        dc = None
+        if xgrad == "kernel" and ctx.needs_input_grad[0]:
+            c, dc = p.execute_grad(f)
+            c, dc = c.reshape(x.shape[1]), dc[0]
+        else:
+            c = p.execute(f).reshape(x.shape[1])
+        ctx.save_for_backward(x, f, dc)
+        ctx.cfg = (n_modes, eps, isign, cache, xgrad)
         return c
 
     @staticmethod
     def backward(ctx, G):
-        x, f = ctx.saved_tensors
-        n_modes, eps, isign, cache = ctx.cfg
+        x, f, dc = ctx.saved_tensors
+        n_modes, eps, isign, cache, xgrad = ctx.cfg
         cdt = _complex_of(x.dtype)
         G = G.contiguous()
         grad_x = grad_f = None
@@ -114,7 +133,9 @@ class _Type2(torch.autograd.Function):
             p1 = cache.get(1, n_modes, eps, -isign, cdt, x.device)
             p1.setpts(*x.unbind(0))
             grad_f = p1.execute(G).reshape(f.shape)
-        if ctx.needs_input_grad[0]:
+        if ctx.needs_input_grad[0] and dc is not None:
+            grad_x = (G.conj().unsqueeze(0) * dc).real
+        elif ctx.needs_input_grad[0]:
             p2 = cache.get(2, n_modes, eps, isign, cdt, x.device)
             p2.setpts(*x.unbind(0))
             rows = []
@@ -122,22 +143,29 @@ class _Type2(torch.autograd.Function):
                 cd = p2.execute(f * _ik(n_modes, d, isign, cdt, x.device)).reshape(G.shape)
                 rows.append((G.conj() * cd).real)
             grad_x = torch.stack(rows)
-        return grad_x, grad_f, None, None, None
+        return grad_x, grad_f, None, None, None, None
+
+
+def _check_xgrad(xgrad):
+    if xgrad not in ("exact", "kernel"):
+        raise ValueError("xgrad must be 'exact' or 'kernel'")
 
 
 def nufft_type1(x: torch.Tensor, c: torch.Tensor, n_modes, eps: float = 1e-6, isign: int = 1,
-                cache: PlanCache | None = None) -> torch.Tensor:
+                cache: PlanCache | None = None, xgrad: str = "exact") -> torch.Tensor:
     """f = F1_s(x) c: x real (d, M) on the GPU, c complex (M,); returns f of shape (N_d, ..., N_1).
-    Differentiable in x and c."""
+    Differentiable in x and c; ``xgrad`` picks the point-gradient route."""
     if x.dim() != 2 or x.shape[0] != len(n_modes):
         raise ValueError("x must have shape (d, M) with d = len(n_modes)")
-    return _Type1.apply(x, c, tuple(int(v) for v in n_modes), eps, isign, cache or _default_cache)
+    _check_xgrad(xgrad)
+    return _Type1.apply(x, c, tuple(int(v) for v in n_modes), eps, isign, cache or _default_cache, xgrad)
 
 
 def nufft_type2(x: torch.Tensor, f: torch.Tensor, eps: float = 1e-6, isign: int = -1,
-                cache: PlanCache | None = None) -> torch.Tensor:
+                cache: PlanCache | None = None, xgrad: str = "exact") -> torch.Tensor:
     """c = F2_s(x) f: x real (d, M), f complex of shape (N_d, ..., N_1); returns c (M,).
-    Differentiable in x and f."""
+    Differentiable in x and f; ``xgrad`` picks the point-gradient route."""
     if x.dim() != 2 or x.shape[0] != f.dim():
         raise ValueError("x must have shape (d, M) with d = f.dim()")
-    return _Type2.apply(x, f, eps, isign, cache or _default_cache)
+    _check_xgrad(xgrad)
+    return _Type2.apply(x, f, eps, isign, cache or _default_cache, xgrad)

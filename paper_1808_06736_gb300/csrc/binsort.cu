@@ -167,26 +167,27 @@ __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict
 // Exclusive scans of the bin counts (-> breakpoints and scatter cursors) and
 // of the per-bin subproblem counts, in one block: the block walks the bins in
 // chunks of blockDim (coalesced), carrying the running totals.
-__device__ __forceinline__ int block_incl_scan(int v, int* wsum) {
+// Inclusive block scan of 64-bit values (1024 threads at most).
+__device__ __forceinline__ long long block_incl_scan(long long v, long long* wsum) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, v, o);
+    long long t = __shfl_up_sync(0xffffffffu, v, o);
     if (lane >= o) v += t;
   }
   if (lane == 31) wsum[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    int u = lane < nw ? wsum[lane] : 0;
+    long long u = lane < nw ? wsum[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, u, o);
+      long long t = __shfl_up_sync(0xffffffffu, u, o);
       if (lane >= o) u += t;
     }
     wsum[lane] = u;
   }
   __syncthreads();
-  int r = v + (wid > 0 ? wsum[wid - 1] : 0);
+  long long r = v + (wid > 0 ? wsum[wid - 1] : 0);
   __syncthreads();  // wsum reused by the next call
   return r;
 }
@@ -202,35 +203,59 @@ __device__ __forceinline__ void split_bin(int c, int maxsub, int smax, int* ntil
   *sparse = sp ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(1024) k_scan(int nbins, int maxsub, int smax, const int* __restrict__ cnt,
-                                               int* __restrict__ start, int* __restrict__ cursor,
-                                               int* __restrict__ sub_first, int* __restrict__ nsub,
-                                               int* __restrict__ nsparse) {
-  __shared__ int wsum[32];
-  __shared__ int carry[2];
-  if (threadIdx.x == 0) carry[0] = carry[1] = 0;
+// One block.  Per round the block stages SCAN_PER * blockDim.x bin counts in
+// shared memory (coalesced), each thread scans SCAN_PER consecutive bins: the
+// point count (high 32 bits) and the tiled-subproblem count (low 32 bits) of
+// its bins go through one 64-bit block scan; the breakpoints are written back
+// through shared memory, again coalesced.
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, int maxsub, int smax, const int* __restrict__ cnt,
+                                                       int* __restrict__ start, int* __restrict__ cursor,
+                                                       int* __restrict__ sub_first, int* __restrict__ nsub,
+                                                       int* __restrict__ nsparse) {
+  constexpr int CHUNK = SCAN_THREADS * SCAN_PER;
+  __shared__ int s_a[CHUNK];  // counts, then point breakpoints
+  __shared__ int s_b[CHUNK];  // subproblem breakpoints
+  __shared__ long long wsum[32];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < nbins; base += blockDim.x) {
-    const int b = base + threadIdx.x;
-    const int c = b < nbins ? cnt[b] : 0;
-    int sc, sp;
-    split_bin(c, maxsub, smax, &sc, &sp);
-    const int cp = carry[0], cs = carry[1];
-    const int ip = block_incl_scan(c, wsum);
-    const int is = block_incl_scan(sc, wsum);
-    if (b < nbins) {
-      start[b] = cp + ip - c;
-      cursor[b] = cp + ip - c;
-      sub_first[b] = cs + is - sc;
+  for (int base = 0; base < nbins; base += CHUNK) {
+    const int len = min(CHUNK, nbins - base);
+    for (int i = threadIdx.x; i < CHUNK; i += blockDim.x) s_a[i] = i < len ? cnt[base + i] : 0;
+    __syncthreads();
+    const int t0 = threadIdx.x * SCAN_PER;
+    int c[SCAN_PER], sc[SCAN_PER];
+    long long tot = 0;
+#pragma unroll
+    for (int u = 0; u < SCAN_PER; ++u) {
+      c[u] = s_a[t0 + u];
+      int sp;
+      split_bin(c[u], maxsub, smax, &sc[u], &sp);
+      tot += ((long long)c[u] << 32) + sc[u];
     }
-    if (threadIdx.x == blockDim.x - 1) {
-      carry[0] = cp + ip;
-      carry[1] = cs + is;
+    const long long cy = carry;
+    long long run = cy + block_incl_scan(tot, wsum) - tot;
+#pragma unroll
+    for (int u = 0; u < SCAN_PER; ++u) {
+      s_a[t0 + u] = (int)(run >> 32);
+      s_b[t0 + u] = (int)(run & 0xffffffffLL);
+      run += ((long long)c[u] << 32) + sc[u];
+    }
+    if (threadIdx.x == blockDim.x - 1) carry = run;
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const int v = s_a[i];
+      start[base + i] = v;
+      cursor[base + i] = v;
+      sub_first[base + i] = s_b[i];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *nsub = carry[1];
+    *nsub = (int)(carry & 0xffffffffLL);
     *nsparse = 0;
   }
 }
@@ -387,7 +412,7 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
   }
   if (ev) cudaEventRecord(ev[1], st);
   const int smax = g.sparse_max < g.maxsub ? g.sparse_max : g.maxsub - 1;
-  k_scan<<<1, 1024, 0, st>>>(nbins, g.maxsub, smax, bin_count, bin_start, cursor, sub_first, nsub, nsparse);
+  k_scan<<<1, SCAN_THREADS, 0, st>>>(nbins, g.maxsub, smax, bin_count, bin_start, cursor, sub_first, nsub, nsparse);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_sublist<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, g.maxsub, smax, bin_count, bin_start, sub_first, nsub,
                                                    nsparse, sub_bin, sub_pt0, sub_cnt);

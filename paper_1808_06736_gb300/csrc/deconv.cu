@@ -4,8 +4,9 @@
 //   for k in I_N -- truncation to the central modes, correction and reordering
 //   in one pass (k_deconv, one thread per output mode).
 // Type 2, step 1 (Sec. 3.2): b^_{k mod n} = p_k f_k for k in I_N and 0 on the
-//   rest of the fine grid (k_precorrect, one thread per fine-grid cell, so the
-//   zero padding and the scatter are a single write of the grid).
+//   rest of the fine grid (a memset of the grid at full write bandwidth, then
+//   k_precorrect, one thread per mode; the batched variant writes every cell
+//   once, one thread per fine-grid cell).
 // p_{k_i} = 2 / (w phi^(alpha_i k_i)) come from the host (Eq. (pk1)) as one
 // array per dimension indexed by k_i + floor(N_i / 2).
 #include "nufft_internal.cuh"
@@ -89,12 +90,37 @@ __global__ void k_deconv(ModeGeom m, const typename Traits<T>::C* __restrict__ g
   for (int row = blockIdx.y; row < nrows; row += gridDim.y) deconv_row<T>(m, row % m.N[1], row / m.N[1], grid, f, p1, p2, p3);
 }
 
+// Scatter of the corrected modes into a zeroed fine grid: one thread per
+// mode, rows of k_1 (the grid's zero padding is a memset beforehand).
+template <typename T>
+__device__ __forceinline__ void scatter_row(const ModeGeom& m, int m2, int m3,
+                                            const typename Traits<T>::C* __restrict__ f,
+                                            typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
+                                            const T* __restrict__ p2, const T* __restrict__ p3) {
+  using C = typename Traits<T>::C;
+  const int k2 = pos_to_k(m2, m.N[1], m.modeord), k3 = pos_to_k(m3, m.N[2], m.modeord);
+  const int l2 = k2 < 0 ? k2 + m.n[1] : k2, l3 = k3 < 0 ? k3 + m.n[2] : k3;
+  const T p23 = p2[k2 + m.N[1] / 2] * p3[k3 + m.N[2] / 2];
+  C* grow = grid + ((long long)l3 * m.n[1] + l2) * (long long)m.n[0];
+  const C* frow = f + ((long long)m3 * m.N[1] + m2) * (long long)m.N[0];
+  for (int m1 = blockIdx.x * blockDim.x + threadIdx.x; m1 < m.N[0]; m1 += gridDim.x * blockDim.x) {
+    const int k1 = pos_to_k(m1, m.N[0], m.modeord);
+    const int l1 = k1 < 0 ? k1 + m.n[0] : k1;
+    const T p = p23 * p1[k1 + m.N[0] / 2];
+    const C v = frow[m1];
+    C o;
+    o.x = v.x * p;
+    o.y = v.y * p;
+    grow[l1] = o;
+  }
+}
+
 template <typename T>
 __global__ void k_precorrect(ModeGeom m, const typename Traits<T>::C* __restrict__ f,
                              typename Traits<T>::C* __restrict__ grid, const T* __restrict__ p1,
                              const T* __restrict__ p2, const T* __restrict__ p3) {
-  const int nrows = m.n[1] * m.n[2];
-  for (int row = blockIdx.y; row < nrows; row += gridDim.y) precorrect_row<T>(m, row % m.n[1], row / m.n[1], f, grid, p1, p2, p3);
+  const int nrows = m.N[1] * m.N[2];
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) scatter_row<T>(m, row % m.N[1], row / m.N[1], f, grid, p1, p2, p3);
 }
 
 // Batched: rows of all transforms in one launch; a row's transform comes from
@@ -160,7 +186,10 @@ cudaError_t deconv_t(const ModeGeom& m, const void* grid, void* f, const void* p
 template <typename T>
 cudaError_t precorrect_t(const ModeGeom& m, const void* f, void* grid, const void* p1,
                          const void* p2, const void* p3, cudaStream_t st) {
-  k_precorrect<T><<<row_grid(m.n[0], m.n[1], m.n[2], 256), 256, 0, st>>>(
+  const size_t bytes = (size_t)m.n[0] * m.n[1] * m.n[2] * sizeof(typename Traits<T>::C);
+  cudaError_t e = cudaMemsetAsync(grid, 0, bytes, st);
+  if (e != cudaSuccess) return e;
+  k_precorrect<T><<<row_grid(m.N[0], m.N[1], m.N[2], 256), 256, 0, st>>>(
       m, (const typename Traits<T>::C*)f, (typename Traits<T>::C*)grid, (const T*)p1, (const T*)p2,
       (const T*)p3);
   return cudaGetLastError();

@@ -1,0 +1,6 @@
+// Instantiation of the interpolation-with-gradient kernels: float, d = 1 (interp_grad.cuh).
+#include "interp_grad.cuh"
+
+namespace nufft {
+NUFFT_DEFINE_GRAD(f32, float, 1)
+}  // namespace nufft

@@ -1,0 +1,6 @@
+// Instantiation of the interpolation-with-gradient kernels: double, d = 2 (interp_grad.cuh).
+#include "interp_grad.cuh"
+
+namespace nufft {
+NUFFT_DEFINE_GRAD(f64, double, 2)
+}  // namespace nufft

@@ -192,6 +192,22 @@ NUFFT_DECL_SI(f64, 2)
 NUFFT_DECL_SI(f64, 3)
 #undef NUFFT_DECL_SI
 
+// --- interpolation with the gradient in the point (interp_grad.cuh) ---------
+struct GradOut {
+  void* dc[3];      // derivative of c_j in x_1, x_2, x_3 (M complex values each)
+  double scale[3];  // (2 / w) n_d / (2 pi)
+};
+#define NUFFT_DECL_GRAD(P, D)                                                                          \
+  cudaError_t interp_grad_##P##_d##D(const Geom&, double, const Sorted&, const void*, void*, const GradOut&, \
+                                     int*, const LaunchCfg&, cudaStream_t, bool);
+NUFFT_DECL_GRAD(f32, 1)
+NUFFT_DECL_GRAD(f32, 2)
+NUFFT_DECL_GRAD(f32, 3)
+NUFFT_DECL_GRAD(f64, 1)
+NUFFT_DECL_GRAD(f64, 2)
+NUFFT_DECL_GRAD(f64, 3)
+#undef NUFFT_DECL_GRAD
+
 // --- deconvolve / pre-correct (deconv.cu) -------------------------------------
 struct ModeGeom {
   int d;
@@ -214,6 +230,7 @@ cudaError_t launch_precorrect_batch(bool dbl, int d, int modeord, long long nrow
 // Execute with the plan's grid, points and cuFFT plan but another type / sign
 // (type 1 on a type-2 plan is its adjoint when isign is flipped).
 int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f);
+int plan_execute_grad(nufft_plan p, void* c, void* dc, const void* f);
 int plan_set_stream(nufft_plan p, cudaStream_t s);
 int plan_reserve(nufft_plan p, int64_t mcap);  // point capacity without setting points
 size_t plan_device_bytes(nufft_plan p);

@@ -50,7 +50,7 @@ struct nufft_plan_s {
   int* sub_cnt = nullptr;
   cufftHandle fft = 0;
   bool fft_ok = false;
-  LaunchCfg spread_cfg{0, 0, 0}, interp_cfg{0, 0, 0};
+  LaunchCfg spread_cfg{0, 0, 0}, interp_cfg{0, 0, 0}, grad_cfg{0, 0, 0};
   cudaEvent_t ev[8];
   bool ev_ok = false;
   int last_steps = 0;  // which timing slots the last call filled: 1 setpts, 2 execute
@@ -266,6 +266,34 @@ static cudaError_t configure(bool spread, bool dbl, const Geom& g, int threads, 
   Sorted s{};
   BatchTable none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
   cudaError_t e = si_dispatch(spread, dbl, g, 0.0, s, nullptr, nullptr, nullptr, *cfg, nullptr, true, none);
+  if (e != cudaSuccess) return e;
+  int per_sm = cfg->blocks, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cfg->blocks = per_sm * sms;
+  return cudaSuccess;
+}
+
+static cudaError_t grad_dispatch(bool dbl, const Geom& g, double beta, const Sorted& s, const void* grid, void* c,
+                                 const GradOut& go, int* work, const LaunchCfg& cfg, cudaStream_t st, bool conf) {
+  if (!dbl) {
+    if (g.d == 1) return interp_grad_f32_d1(g, beta, s, grid, c, go, work, cfg, st, conf);
+    if (g.d == 2) return interp_grad_f32_d2(g, beta, s, grid, c, go, work, cfg, st, conf);
+    return interp_grad_f32_d3(g, beta, s, grid, c, go, work, cfg, st, conf);
+  }
+  if (g.d == 1) return interp_grad_f64_d1(g, beta, s, grid, c, go, work, cfg, st, conf);
+  if (g.d == 2) return interp_grad_f64_d2(g, beta, s, grid, c, go, work, cfg, st, conf);
+  return interp_grad_f64_d3(g, beta, s, grid, c, go, work, cfg, st, conf);
+}
+
+static cudaError_t grad_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg) {
+  cfg->threads = threads;
+  cfg->smem = interp_smem_bytes(dbl, g, threads);
+  cfg->blocks = 0;
+  Sorted s{};
+  GradOut go{};
+  cudaError_t e = grad_dispatch(dbl, g, 0.0, s, nullptr, nullptr, go, nullptr, *cfg, nullptr, true);
   if (e != cudaSuccess) return e;
   int per_sm = cfg->blocks, dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -515,6 +543,53 @@ int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f) {
   return NUFFT_OK;
 }
 
+int plan_execute_grad(nufft_plan p, void* c, void* dc, const void* f) {
+  if (!p || p->type != 2) return NUFFT_ERR_BAD_ARG;
+  if (p->M < 0) return NUFFT_ERR_NOT_SET;
+  if (!f || (p->M > 0 && (!c || !dc))) return NUFFT_ERR_BAD_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
+  const Geom& g = p->g;
+  if (p->grad_cfg.blocks == 0) {
+    int threads = p->opts.threads > 0 ? p->opts.threads : 256;
+    if (grad_config(p->dbl, g, threads, &p->grad_cfg) != cudaSuccess) return NUFFT_ERR_CUDA;
+  }
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
+  ModeGeom mg;
+  mg.d = p->dim;
+  mg.modeord = p->opts.modeord ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    mg.N[i] = (int)p->N[i];
+    mg.n[i] = g.n[i];
+  }
+  const int dir = p->isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
+  const double two_pi = 6.283185307179586476925286766559;
+  cudaEvent_t* ev = p->ev_ok ? p->ev + 4 : nullptr;
+  for (int t = 0; t < p->ntransf; ++t) {
+    char* ct = (char*)c + (size_t)t * (size_t)p->M * p->csize;
+    char* dct = (char*)dc + (size_t)t * (size_t)p->dim * (size_t)p->M * p->csize;
+    const char* ft = (const char*)f + (size_t)t * (size_t)p->Ntot * p->csize;
+    if (ev && t == 0) cudaEventRecord(ev[0], p->stream);
+    CUDA_TRY(launch_precorrect(p->dbl, mg, ft, p->grid, p->pk[0], p->pk[1], p->pk[2], p->stream));
+    if (ev && t == 0) cudaEventRecord(ev[1], p->stream);
+    cufftResult r = p->dbl ? cufftExecZ2Z(p->fft, (cufftDoubleComplex*)p->grid, (cufftDoubleComplex*)p->grid, dir)
+                           : cufftExecC2C(p->fft, (cufftComplex*)p->grid, (cufftComplex*)p->grid, dir);
+    if (r != CUFFT_SUCCESS) return NUFFT_ERR_CUFFT;
+    if (ev && t == 0) cudaEventRecord(ev[2], p->stream);
+    if (p->M > 0) {
+      CUDA_TRY(cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream));
+      GradOut go{};
+      for (int d = 0; d < 3; ++d) {
+        go.dc[d] = d < p->dim ? dct + (size_t)d * (size_t)p->M * p->csize : nullptr;
+        go.scale[d] = d < p->dim ? (2.0 / p->w) * ((double)g.n[d] / two_pi) : 0.0;
+      }
+      CUDA_TRY(grad_dispatch(p->dbl, g, p->beta, s, p->grid, ct, go, p->small + 2, p->grad_cfg, p->stream, false));
+    }
+    if (ev && t == 0) cudaEventRecord(ev[3], p->stream);
+  }
+  p->last_steps = 2;
+  return NUFFT_OK;
+}
+
 int plan_set_stream(nufft_plan p, cudaStream_t s) {
   if (!p) return NUFFT_ERR_BAD_ARG;
   p->stream = s;
@@ -604,6 +679,10 @@ int plan_modes(nufft_plan p, int64_t* N, int* dim) {
 }  // namespace nufft
 
 extern "C" {
+
+int nufft_execute_grad(nufft_plan p, void* c, void* dc, const void* f) {
+  return nufft::plan_execute_grad(p, c, dc, f);
+}
 
 int nufft_destroy(nufft_plan p) {
   if (!p) return NUFFT_OK;

@@ -16,7 +16,9 @@
 //   grad_f = 2 F1_{-s}(x) (c - y)                 (the adjoint, Sec. 1),
 //   grad_x_{j,d} = 2 Re( conj(c_j - y_j) (F2_s(x) [(s i k_d) f])_j ),
 // the last being the exact derivative of the exponential sum, formed as one
-// more type-2 transform per dimension on the same sorted points.
+// more type-2 transform per dimension on the same sorted points, or (flag
+// NUFFT_FLAG_XGRAD_KERNEL) taken from the first transform's interpolation
+// differentiated through the ES kernel (nufft_execute_grad).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -146,7 +148,7 @@ Key key_of(const nufft_request* r) {
 struct GpuEntry {
   nufft_plan p = nullptr;
   int kind = 0;
-  void* cbuf = nullptr;  // LSQ: c, then each c_d
+  void* cbuf = nullptr;  // LSQ: c, then each c_d (exact route) or the dim rows of dc (kernel route)
   void* r2 = nullptr;    // LSQ: 2 (c - y)
   void* fk = nullptr;    // LSQ: (s i k_d) f
 };
@@ -170,7 +172,7 @@ struct GpuExecutor {
   static size_t scratch_bytes(const nufft_request* r, int64_t mcap) {
     if (r->kind != NUFFT_REQ_LSQ_GRAD) return 0;
     size_t cs = r->prec == NUFFT_C128 ? 16 : 8;
-    return (2 * (size_t)mcap + (size_t)ntot_of(r)) * cs;
+    return ((2 + (size_t)r->dim) * (size_t)mcap + (size_t)ntot_of(r)) * cs;
   }
 
   static int estimate(void*, const nufft_request* r, int64_t mcap, size_t* bytes) {
@@ -209,7 +211,7 @@ struct GpuExecutor {
     }
     size_t cs = r->prec == NUFFT_C128 ? 16 : 8;
     if (r->kind == NUFFT_REQ_LSQ_GRAD) {
-      if (cudaMalloc(&e->cbuf, std::max<size_t>(16, (size_t)mcap * cs)) != cudaSuccess ||
+      if (cudaMalloc(&e->cbuf, std::max<size_t>(16, (1 + (size_t)r->dim) * (size_t)mcap * cs)) != cudaSuccess ||
           cudaMalloc(&e->r2, std::max<size_t>(16, (size_t)mcap * cs)) != cudaSuccess ||
           cudaMalloc(&e->fk, (size_t)ntot_of(r) * cs) != cudaSuccess) {
         free_entry(e);
@@ -226,7 +228,9 @@ struct GpuExecutor {
     const int s = r->isign;
     const int64_t M = r->M;
     const int64_t ntot = ntot_of(r);
-    int rc = plan_execute_as(e->p, 2, s, e->cbuf, (void*)r->in);
+    const bool kern = (r->flags & NUFFT_FLAG_XGRAD_KERNEL) != 0;
+    C2<T>* dcb = (C2<T>*)e->cbuf + M;  // kernel route: dc rows after c
+    int rc = kern ? plan_execute_grad(e->p, e->cbuf, dcb, r->in) : plan_execute_as(e->p, 2, s, e->cbuf, (void*)r->in);
     if (rc != NUFFT_OK) return rc;
     if (cudaMemsetAsync(r->out3, 0, sizeof(double), st) != cudaSuccess) return NUFFT_ERR_CUDA;
     if (M > 0) {
@@ -237,6 +241,13 @@ struct GpuExecutor {
     rc = plan_execute_as(e->p, 1, -s, e->r2, r->out);
     if (rc != NUFFT_OK) return rc;
     if (M == 0) return NUFFT_OK;
+    if (kern) {
+      for (int d = 0; d < r->dim; ++d) {
+        k_gradx<T><<<grid1d(M), 256, 0, st>>>(M, (const C2<T>*)e->r2, dcb + d * M, (T*)r->out2 + d * M);
+        if (cudaGetLastError() != cudaSuccess) return NUFFT_ERR_CUDA;
+      }
+      return NUFFT_OK;
+    }
     int64_t N[3] = {1, 1, 1};
     for (int i = 0; i < r->dim; ++i) N[i] = r->nmodes[i];
     for (int d = 0; d < r->dim; ++d) {

@@ -17,13 +17,14 @@ from . import NufftError, NUFFT_C64, NUFFT_C128, _L as _base_lib
 NUFFT_REQ_TYPE1 = 1
 NUFFT_REQ_TYPE2 = 2
 NUFFT_REQ_LSQ_GRAD = 3
+NUFFT_FLAG_XGRAD_KERNEL = 1
 NUFFT_ERR_TIMEOUT = -8
 NUFFT_ERR_REJECTED = -9
 NUFFT_ERR_SHUTDOWN = -10
 
 
 class nufft_request(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int), ("nmodes", ctypes.c_int64 * 3),
+    _fields_ = [("kind", ctypes.c_int), ("flags", ctypes.c_int), ("dim", ctypes.c_int), ("nmodes", ctypes.c_int64 * 3),
                 ("isign", ctypes.c_int), ("prec", ctypes.c_int), ("eps", ctypes.c_double), ("M", ctypes.c_int64),
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("in_", ctypes.c_void_p), ("in2", ctypes.c_void_p), ("out", ctypes.c_void_p),
@@ -138,8 +139,9 @@ def nufft_request_bytes(req: nufft_request, mcap: int):
 
 
 def make_request(kind: int, dim: int, n_modes, isign: int, prec: int, eps: float, M: int, tag: int = 0,
-                 points_key: int = 0) -> nufft_request:
+                 points_key: int = 0, flags: int = 0) -> nufft_request:
     r = nufft_request()
+    r.flags = int(flags)
     r.kind, r.dim, r.isign, r.prec, r.eps, r.M = int(kind), int(dim), int(isign), int(prec), float(eps), int(M)
     for i, v in enumerate(n_modes):
         r.nmodes[i] = int(v)
@@ -199,7 +201,7 @@ class Server:
             xs = list(x)
         return [torch.as_tensor(v).to(device=self.device, dtype=rdt).contiguous() for v in xs]
 
-    def _submit(self, kind, xs, data, n_modes, eps, isign, dtype, y=None, points_key=0, tag=0):
+    def _submit(self, kind, xs, data, n_modes, eps, isign, dtype, y=None, points_key=0, tag=0, flags=0):
         torch = self._torch
         cdt = dtype
         rdt = torch.float32 if cdt == torch.complex64 else torch.float64
@@ -209,7 +211,7 @@ class Server:
             d = len(xs)
             M = xs[0].numel()
             data = torch.as_tensor(data).to(device=self.device, dtype=cdt).contiguous()
-            r = make_request(kind, d, n_modes, isign, prec, eps, M, tag=tag, points_key=points_key)
+            r = make_request(kind, d, n_modes, isign, prec, eps, M, tag=tag, points_key=points_key, flags=flags)
             ptr = [v.data_ptr() for v in xs] + [0] * (3 - d)
             r.x, r.y, r.z = ptr
             r.in_ = data.data_ptr()
@@ -249,12 +251,15 @@ class Server:
         n_modes = tuple(reversed(f.shape))
         return self._submit(NUFFT_REQ_TYPE2, x, f, n_modes, eps, isign, dtype, points_key=points_key, tag=tag)
 
-    def lsq_grad(self, x, f, y, eps=1e-6, isign=-1, dtype=None, points_key=0, tag=0):
-        """loss = ||F2_isign(f; x) - y||^2 with its gradients in f and in the points."""
+    def lsq_grad(self, x, f, y, eps=1e-6, isign=-1, dtype=None, points_key=0, tag=0, xgrad="exact"):
+        """loss = ||F2_isign(f; x) - y||^2 with its gradients in f and in the points
+        (``xgrad``: "exact" or "kernel", as in the autograd functions)."""
+        if xgrad not in ("exact", "kernel"):
+            raise ValueError("xgrad must be 'exact' or 'kernel'")
         dtype = dtype or self._torch.complex64
         n_modes = tuple(reversed(f.shape))
         return self._submit(NUFFT_REQ_LSQ_GRAD, x, f, n_modes, eps, isign, dtype, y=y, points_key=points_key,
-                            tag=tag)
+                            tag=tag, flags=NUFFT_FLAG_XGRAD_KERNEL if xgrad == "kernel" else 0)
 
     def poll(self, max_n: int = 256, wait_s: float = 0.0):
         st, cs = nufft_server_poll(self._h, max_n, wait_s)

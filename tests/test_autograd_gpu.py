@@ -28,8 +28,12 @@ def _k(Ns):
     return [g.ravel() for g in reversed(grids)]
 
 
-@pytest.mark.parametrize("cdt,eps,tol", [("c128", 1e-11, 1e-9), ("c64", 1e-5, 1e-4)])
-def test_type2_loss_gradients_3d(ag, oracle_mod, cdt, eps, tol):
+# "exact": the point gradient through d extra transforms of (i k_d) f, bar 10 eps;
+# "kernel": through the derivative of the ES kernel, whose error is ~2 sqrt(12) times the
+# values' (aliased frequencies weighted by their own size), bar 20 eps with an fp32 floor.
+@pytest.mark.parametrize("cdt,eps,tol,xgrad", [("c128", 1e-11, 1e-9, "exact"), ("c64", 1e-5, 1e-4, "exact"),
+                                               ("c128", 1e-11, 2e-10, "kernel"), ("c64", 1e-5, 2e-4, "kernel")])
+def test_type2_loss_gradients_3d(ag, oracle_mod, cdt, eps, tol, xgrad):
     """3D, N = 64^3, M = 1e5: grad wrt f on sampled modes, wrt x on sampled points."""
     import torch
     dev = torch.device("cuda:0")
@@ -41,7 +45,7 @@ def test_type2_loss_gradients_3d(ag, oracle_mod, cdt, eps, tol):
     f = torch.tensor(I.complex_normal(62, 64 ** 3).reshape(64, 64, 64), dtype=cdtype, device=dev,
                      requires_grad=True)
     y = torch.tensor(I.complex_normal(63, M), dtype=cdtype, device=dev)
-    c = ag.nufft_type2(x, f, eps=eps, isign=-1)
+    c = ag.nufft_type2(x, f, eps=eps, isign=-1, xgrad=xgrad)
     loss = ((c - y).abs() ** 2).sum()
     loss.backward()
     xs = [v.astype(np.float64) for v in x.detach().cpu().numpy()]
@@ -65,8 +69,9 @@ def test_type2_loss_gradients_3d(ag, oracle_mod, cdt, eps, tol):
     assert np.linalg.norm(got_f - ref_f) <= tol * np.linalg.norm(ref_f)
 
 
+@pytest.mark.parametrize("xgrad", ["exact", "kernel"])
 @pytest.mark.parametrize("typ", [1, 2])
-def test_point_gradient_matches_finite_differences(ag, typ):
+def test_point_gradient_matches_finite_differences(ag, typ, xgrad):
     """Central differences of the GPU loss (complex128, eps = 1e-13) in a few coordinates."""
     import torch
     dev = torch.device("cuda:0")
@@ -81,9 +86,9 @@ def test_point_gradient_matches_finite_differences(ag, typ):
 
     def loss(xt):
         if typ == 1:
-            out = ag.nufft_type1(xt, c, Ns, eps=eps, isign=1)
+            out = ag.nufft_type1(xt, c, Ns, eps=eps, isign=1, xgrad=xgrad)
             return ((out - y1).abs() ** 2).sum()
-        out = ag.nufft_type2(xt, f, eps=eps, isign=-1)
+        out = ag.nufft_type2(xt, f, eps=eps, isign=-1, xgrad=xgrad)
         return ((out - y2).abs() ** 2).sum()
 
     x = torch.tensor(x0, device=dev, requires_grad=True)

@@ -249,3 +249,56 @@ def test_sparse_subproblems(pkg, oracle_mod, cdtype, eps, d, kind):
         assert oracle_mod.rel_l2(g2[0], o1_2) <= bar
         assert oracle_mod.rel_l2(g1[0], ref1[0]) <= TOL_SAME[cdtype]
         assert oracle_mod.rel_l2(g2[0], ref2[0]) <= TOL_SAME[cdtype]
+
+
+GRAD_SIZES = {1: ([400], 3000), 2: ([40, 36], 6000), 3: ([16, 14, 12], 8000)}
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex64, 1e-3), (np.complex128, 1e-9)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("density", ["dense", "sparse"])
+def test_execute_grad_against_direct_sum_derivative(pkg, oracle_mod, cdtype, eps, d, density):
+    """nufft_execute_grad: values as nufft_execute, and dc_j/dx_{j,d} against the FP64
+    derivative of the exact sum, sum_k f_k (i isign k_d) exp(i isign k.x_j).
+
+    Bar for the derivative: differentiating the interpolant weights each aliased
+    frequency k + m n (|m| >= 1, |k + m n| ~ n = 2N) by its own size, against an RMS
+    mode frequency N / sqrt(12) for the exact derivative, so its relative error is
+    about 2 sqrt(12) ~ 7 times that of the values; with the values' bar of 10 eps
+    and their typical error of 1-2 eps, the bar is 20 eps (fp32: at least 2e-4)."""
+    import torch
+    Ns, M = GRAD_SIZES[d]
+    if density == "sparse":
+        Ns = [4 * v for v in Ns] if d < 3 else [2 * v for v in Ns]
+        M = M // 8
+    xs, _, f = case_inputs(d, Ns, M, "uniform", cdtype, seed=4000 + 10 * d)
+    x64 = [v.astype(np.float64) for v in xs]
+    dev = torch.device("cuda:0")
+    tdt = torch.complex64 if cdtype == np.complex64 else torch.complex128
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    isign = -1
+    p = pkg.Plan(2, Ns, eps=eps, isign=isign, dtype=tdt, device=dev)
+    p.setpts(*[torch.from_numpy(np.ascontiguousarray(v, dtype=rdt)).to(dev) for v in xs])
+    fd = torch.from_numpy(np.ascontiguousarray(f, dtype=cdtype)).to(dev)
+    c, dc = p.execute_grad(fd)
+    c0 = p.execute(fd)
+    assert p.status() == 0
+    p.close()
+    c, dc, c0 = c.cpu().numpy()[0], dc.cpu().numpy()[0], c0.cpu().numpy()[0]
+    assert oracle_mod.rel_l2(c, c0) <= TOL_SAME[cdtype]
+    fn = f.astype(np.complex128).ravel()
+    assert oracle_mod.rel_l2(c, oracle_mod.direct_type2(x64, fn, isign, Ns)) <= 10 * max(eps, 2e-6 if cdtype == np.complex64 else 0)
+    grids = np.meshgrid(*[np.arange(n) - n // 2 for n in reversed(Ns)], indexing="ij")
+    ks = [g.ravel() for g in reversed(grids)]
+    bar = 20 * max(eps, 1e-5 if cdtype == np.complex64 else 0)
+    for k in range(d):
+        ref = oracle_mod.direct_type2(x64, fn * (1j * isign * ks[k]), isign, Ns)
+        assert oracle_mod.rel_l2(dc[k], ref) <= bar, (k, oracle_mod.rel_l2(dc[k], ref))
+
+
+def test_execute_grad_rejects_type1_plan(pkg):
+    import torch
+    p = pkg.Plan(1, [16, 16], eps=1e-5, device="cuda:0")
+    p.setpts(torch.zeros(10, device="cuda:0"), torch.zeros(10, device="cuda:0"))
+    assert pkg.nufft_execute_grad(p._h, 1, 1, 1) == -1
+    p.close()

@@ -314,5 +314,5 @@ def test_request_bytes_estimate_counts_grid_and_points():
     assert b2 - b >= 131072 * 16
     r3 = S.make_request(3, 3, (64, 64, 64), -1, 1, 1e-5, 100000)
     st, b3 = S.nufft_request_bytes(r3, 131072)
-    assert b3 - b == (2 * 131072 + 64 ** 3) * 8  # gradient scratch
+    assert b3 - b == ((2 + 3) * 131072 + 64 ** 3) * 8  # gradient scratch
     assert S.nufft_request_bytes(r, 10)[0] == -1  # capacity below M
