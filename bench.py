@@ -434,6 +434,25 @@ def run_batched2d(args):
     ms_b = e0.elapsed_time(e1) / args.steps
     assert bp.status() == 0
 
+    # autotuned batch plan (bin shape, subproblem size, sparse threshold, block size)
+    t_tune = time.time()
+    opts, tune_best, tune_default = pkg.tune_batch(2, modes, xs, f, offs, eps=args.eps, isign=-1, reps=2)
+    t_tune = time.time() - t_tune
+    bt = pkg.BatchPlan(2, modes, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev, **opts)
+    for _ in range(args.warmup):
+        bt.setpts(*xs, offsets=offs)
+        bt.execute(f, out=cout)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.setpts(*xs, offsets=offs)
+        bt.execute(f, out=cout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / args.steps
+    assert bt.status() == 0
+    bt.close()
+
     plans = [pkg.Plan(2, m, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev) for m in modes]
     moffs = bp.mode_offsets
     couts = [cout[int(offs[t]):int(offs[t + 1])] for t in range(B)]
@@ -457,14 +476,18 @@ def run_batched2d(args):
     for p in plans:
         p.close()
     bp.close()
+    ms_best = min(ms_b, ms_t)
     line = {"metric": "batched 2D type-2 NU points/s (%d transforms, eps=%g, fp32)" % (B, args.eps),
-            "value": Mtot / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "value": Mtot / (ms_best * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_best, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "batched2d", "transforms": B, "modes": "uniform in {64,128,256,512}^2",
                        "M": "log-uniform in [1e3, 1e6]", "points_total": Mtot, "step": "setpts + execute of all"},
+            "default_options": {"value": Mtot / (ms_b * 1e-3), "ms_per_step": ms_b},
+            "autotuned": {"value": Mtot / (ms_t * 1e-3), "ms_per_step": ms_t, "options": opts,
+                          "tuner_best_ms": tune_best, "tuner_default_ms": tune_default, "tuning_s": t_tune},
             "plain": {"value": Mtot / (ms_p * 1e-3), "ms_per_step": ms_p, "path": "one Plan per transform"},
-            "speedup_vs_plain": ms_p / ms_b}
+            "speedup_vs_plain": ms_p / ms_best}
     print(json.dumps(line))
     return 0
 

@@ -230,6 +230,35 @@ int nufft_batch_get_status(nufft_batch plan);
 /* Free everything; NULL is accepted. */
 int nufft_batch_destroy(nufft_batch plan);
 
+/* ---------------------------------------------------------------- autotuning
+ * Time launch configurations on the caller's own points and data and return
+ * the fastest as options for nufft_makeplan / nufft_batch_makeplan: the bin
+ * extents (hence the shared-memory tile, bin + w per dimension; 1D 256..4096,
+ * 2D {8,16,32,64}^2, 3D B1 >= B2 >= B3 in {4,8,16,32}, those whose tile fits
+ * in shared memory), the largest subproblem (max_subprob 256..4096), the
+ * per-warp threshold (sparse_max -1, 8, 16, default 32) and the threads per
+ * block (128, default 256).  Staged search: bins first, then each further
+ * tunable from the best so far; the default options are timed first, so
+ * *best_ms <= *default_ms.  A configuration is timed as one untimed setpts +
+ * execute, then reps timed ones (CUDA events on stream; the minimum counts);
+ * each trial makes and destroys its own plan.  in / out are the transform's
+ * input and a scratch output (type 1: c and f; type 2: f and c), device
+ * memory; for the batch variant offsets, x, y, z, in and out are as for
+ * nufft_batch_setpts / nufft_batch_execute.  best_ms / default_ms may be
+ * NULL.  Returns NUFFT_OK, BAD_ARG, or CUDA when even the default fails.
+ */
+int nufft_tune(int type, int dim, const int64_t* nmodes, int isign, double eps, int prec, int64_t M, const void* x,
+               const void* y, const void* z, const void* in, void* out, void* stream, int reps, nufft_opts* best,
+               double* best_ms, double* default_ms);
+int nufft_batch_tune(int type, int dim, int B, const int64_t* nmodes, int isign, double eps, int prec,
+                     const int64_t* offsets, const void* x, const void* y, const void* z, const void* in, void* out,
+                     void* stream, int reps, nufft_opts* best, double* best_ms, double* default_ms);
+
+/* Host-only: the bin shapes the tuner tries for this dimension, precision and
+ * kernel width, written to bins (3 ints each, at most max shapes); returns
+ * how many there are, or NUFFT_ERR_BAD_ARG. */
+int nufft_tune_candidates(int dim, int prec, int w, int* bins, int max);
+
 /* ------------------------------------------------------------ no allocation
  * nufft_spread_noalloc -- the spreading step of a complex64 type-1 transform
  * (fine-grid values b_l of Eq. (bl)) for callers that cannot allocate device

@@ -20,7 +20,8 @@ __all__ = [
     "nufft_execute", "nufft_execute_grad", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
     "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235",
     "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
-    "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy",
+    "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy", "nufft_tune", "nufft_batch_tune",
+    "nufft_tune_candidates", "opts_dict", "tune_plan", "tune_batch",
     "NUFFT_C64", "NUFFT_C128",
 ]
 
@@ -86,6 +87,12 @@ def _L():
     lib.nufft_batch_execute.argtypes = [vp, vp, vp]
     lib.nufft_batch_get_status.argtypes = [vp]
     lib.nufft_batch_destroy.argtypes = [vp]
+    pd = ctypes.POINTER(ctypes.c_double)
+    lib.nufft_tune.argtypes = [i32, i32, pi64, i32, dbl, i32, i64, vp, vp, vp, vp, vp, vp, i32,
+                               ctypes.POINTER(nufft_opts), pd, pd]
+    lib.nufft_batch_tune.argtypes = [i32, i32, i32, pi64, i32, dbl, i32, pi64, vp, vp, vp, vp, vp, vp, i32,
+                                     ctypes.POINTER(nufft_opts), pd, pd]
+    lib.nufft_tune_candidates.argtypes = [i32, i32, i32, ctypes.POINTER(i32), i32]
     _lib = lib
     return lib
 
@@ -203,6 +210,49 @@ def nufft_batch_get_status(plan) -> int:
 
 def nufft_batch_destroy(plan) -> int:
     return _L().nufft_batch_destroy(plan)
+
+
+def nufft_tune_candidates(dim: int, prec: int, w: int):
+    n = _L().nufft_tune_candidates(int(dim), int(prec), int(w), None, 0)
+    if n < 0:
+        return n, []
+    buf = (ctypes.c_int * (3 * max(n, 1)))()
+    _L().nufft_tune_candidates(int(dim), int(prec), int(w), buf, n)
+    return n, [tuple(buf[3 * k:3 * k + 3]) for k in range(n)]
+
+
+def nufft_tune(type_: int, dim: int, nmodes, isign: int, eps: float, prec: int, M: int, x: int, y: int, z: int,
+               inp: int, out: int, stream: int | None, reps: int = 3):
+    """Returns (status, best nufft_opts, best ms, default ms)."""
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in nmodes] + [1] * (3 - len(nmodes))))
+    o = nufft_opts()
+    b, d = ctypes.c_double(), ctypes.c_double()
+    vp = ctypes.c_void_p
+    st = _L().nufft_tune(int(type_), int(dim), arr, int(isign), float(eps), int(prec), int(M), vp(x or 0), vp(y or 0),
+                         vp(z or 0), vp(inp or 0), vp(out or 0), vp(stream or 0), int(reps), ctypes.byref(o),
+                         ctypes.byref(b), ctypes.byref(d))
+    return st, o, b.value, d.value
+
+
+def nufft_batch_tune(type_: int, dim: int, nmodes, isign: int, eps: float, prec: int, offsets, x: int, y: int,
+                     z: int, inp: int, out: int, stream: int | None, reps: int = 3):
+    """nmodes: list of B mode-count tuples.  Returns (status, best nufft_opts, best ms, default ms)."""
+    flat = [int(v) for m in nmodes for v in m]
+    arr = (ctypes.c_int64 * len(flat))(*flat)
+    offs = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+    o = nufft_opts()
+    b, d = ctypes.c_double(), ctypes.c_double()
+    vp = ctypes.c_void_p
+    st = _L().nufft_batch_tune(int(type_), int(dim), len(nmodes), arr, int(isign), float(eps), int(prec), offs,
+                               vp(x or 0), vp(y or 0), vp(z or 0), vp(inp or 0), vp(out or 0), vp(stream or 0),
+                               int(reps), ctypes.byref(o), ctypes.byref(b), ctypes.byref(d))
+    return st, o, b.value, d.value
+
+
+def opts_dict(o: nufft_opts) -> dict:
+    """The tunable fields of an options struct, as keyword arguments for Plan / BatchPlan."""
+    return {"bin_size": tuple(o.bin_size), "max_subprob": o.max_subprob, "threads": o.threads,
+            "sparse_max": o.sparse_max}
 
 
 # --------------------------------------------------------------- torch layer
@@ -462,3 +512,64 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def tune_plan(nufft_type: int, n_modes, x, data, eps: float = 1e-6, isign: int | None = None, dtype=None,
+              device=None, reps: int = 3):
+    """Autotune a plan on these points and this input (nufft_tune).  x: list of d
+    coordinate tensors; data: c (type 1) or f (type 2).  Returns (options for
+    Plan(**opts), best ms, default ms) for one setpts + execute."""
+    import torch
+    dtype = dtype if dtype is not None else torch.complex64
+    dev = torch.device(device if device is not None else "cuda")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    rdt = torch.float32 if dtype == torch.complex64 else torch.float64
+    prec = NUFFT_C64 if dtype == torch.complex64 else NUFFT_C128
+    isign = int(isign) if isign is not None else (1 if nufft_type == 1 else -1)
+    xs = [torch.as_tensor(v).to(device=dev, dtype=rdt).contiguous() for v in x]
+    d = torch.as_tensor(data).to(device=dev, dtype=dtype).contiguous()
+    M = xs[0].numel()
+    Nt = 1
+    for v in n_modes:
+        Nt *= int(v)
+    out = torch.empty(Nt if nufft_type == 1 else M, dtype=dtype, device=dev)
+    ptrs = [v.data_ptr() for v in xs] + [0] * (3 - len(xs))
+    with torch.cuda.device(dev):
+        st, o, best, default = nufft_tune(nufft_type, len(xs), n_modes, isign, eps, prec, M, *ptrs, d.data_ptr(),
+                                          out.data_ptr(), torch.cuda.current_stream(dev).cuda_stream, reps)
+    if st < 0:
+        raise NufftError(st, "nufft_tune")
+    return opts_dict(o), best, default
+
+
+def tune_batch(nufft_type: int, modes, x, data, offsets, eps: float = 1e-6, isign: int | None = None, dtype=None,
+               device=None, reps: int = 3):
+    """Autotune a BatchPlan (nufft_batch_tune); arguments as BatchPlan.setpts / execute.
+    Returns (options for BatchPlan(**opts), best ms, default ms)."""
+    import torch
+    dtype = dtype if dtype is not None else torch.complex64
+    dev = torch.device(device if device is not None else "cuda")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    rdt = torch.float32 if dtype == torch.complex64 else torch.float64
+    prec = NUFFT_C64 if dtype == torch.complex64 else NUFFT_C128
+    isign = int(isign) if isign is not None else (1 if nufft_type == 1 else -1)
+    xs = [torch.as_tensor(v).to(device=dev, dtype=rdt).contiguous() for v in x]
+    d = torch.as_tensor(data).to(device=dev, dtype=dtype).contiguous()
+    M = xs[0].numel()
+    total_modes = 0
+    for m in modes:
+        t = 1
+        for v in m:
+            t *= int(v)
+        total_modes += t
+    out = torch.empty(total_modes if nufft_type == 1 else M, dtype=dtype, device=dev)
+    ptrs = [v.data_ptr() for v in xs] + [0] * (3 - len(xs))
+    with torch.cuda.device(dev):
+        st, o, best, default = nufft_batch_tune(nufft_type, len(xs), modes, isign, eps, prec, offsets, *ptrs,
+                                                d.data_ptr(), out.data_ptr(),
+                                                torch.cuda.current_stream(dev).cuda_stream, reps)
+    if st < 0:
+        raise NufftError(st, "nufft_batch_tune")
+    return opts_dict(o), best, default

@@ -88,3 +88,23 @@ def test_make_plan_validates_before_device_use(lib):
     assert lib.nufft_setpts(None, 10, 0, 0, 0) == -1
     assert lib.nufft_execute(None, 0, 0) == -1
     assert lib.nufft_destroy(None) == 0
+
+
+def test_tune_candidates_host_only(lib):
+    for d, default in ((1, (1024, 1, 1)), (2, (32, 32, 1)), (3, (16, 8, 8))):
+        for prec in (lib.NUFFT_C64, lib.NUFFT_C128):
+            n, shapes = lib.nufft_tune_candidates(d, prec, 6)
+            assert n == len(shapes) and n >= 5
+            assert default in shapes
+            for b in shapes:
+                assert all(v == 1 for v in b[d:])
+                if d == 1:
+                    assert 256 <= b[0] <= 4096
+                elif d == 2:
+                    assert all(8 <= v <= 64 for v in b[:2])
+                else:
+                    assert all(4 <= v <= 32 for v in b) and b[0] >= b[1] >= b[2]
+    # wider kernels leave fewer tiles that fit in shared memory
+    assert lib.nufft_tune_candidates(3, lib.NUFFT_C128, 16)[0] < lib.nufft_tune_candidates(3, lib.NUFFT_C64, 2)[0]
+    assert lib.nufft_tune_candidates(4, lib.NUFFT_C64, 6)[0] == -1
+    assert lib.nufft_tune_candidates(2, lib.NUFFT_C64, 17)[0] == -1
