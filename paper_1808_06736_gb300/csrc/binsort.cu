@@ -135,10 +135,16 @@ __device__ __forceinline__ int point_bin_batch(const Geom& g0, const BatchTable&
   return tg.boff + bin_id(g, b[0], b[1], b[2]);
 }
 
+// Bin counters come in nrep replicas (a power of two): point j counts in
+// replica j mod nrep, so a crowded bin's increments go to nrep addresses
+// instead of one (same-address atomics serialise at the L2: a bin holding
+// 0.5% of 1e8 clustered points would otherwise take milliseconds alone).
+// The replicas are summed per bin before the scan; in crowded bins each
+// replica then gets its own scatter cursor inside the bin's range.
 template <typename T>
 __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict__ y,
                              const T* __restrict__ z, Geom g, FoldConst fc, int chk,
-                             int* __restrict__ bin_count, int* __restrict__ err, BatchTable bt) {
+                             int* __restrict__ rep_count, int nrep, int nbins, int* __restrict__ err, BatchTable bt) {
   const int stride = gridDim.x * blockDim.x;
   bool bad = false;
   for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += kILP * stride) {
@@ -157,7 +163,7 @@ __global__ void k_fold_count(int M, const T* __restrict__ x, const T* __restrict
       const int j = j0 + u * stride;
       if (j < M) {
         const int bin = bt.B > 0 ? point_bin_batch(g, bt, j, v[u], chk, &bad) : point_bin(g, fc, v[u], chk, &bad);
-        atomicAdd(&bin_count[bin], 1);  // result unused
+        atomicAdd(&rep_count[(size_t)(j & (nrep - 1)) * nbins + bin], 1);  // result unused
       }
     }
   }
@@ -296,10 +302,51 @@ __global__ void k_sublist(int nbins, int maxsub, int smax, const int* __restrict
   }
 }
 
+__global__ void k_rep_sum(int nbins, int nrep, const int* __restrict__ rep_count, int* __restrict__ bin_count) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+    int t = 0;
+    for (int r = 0; r < nrep; ++r) t += rep_count[(size_t)r * nbins + b];
+    bin_count[b] = t;
+  }
+}
+
+// Only crowded bins scatter through their replica cursors; every other bin
+// keeps one cursor (replica 0), so its records are written in arrival order
+// into one range and its cursor stays hot in L2.
+constexpr int kCrowded = 4096;
+
+// Replica r of a crowded bin b starts after replicas 0..r-1 inside the bin's
+// range; crowded bins are also marked in a bit mask (zeroed beforehand).
+__global__ void k_rep_cursor(int nbins, int nrep, const int* __restrict__ rep_count, const int* __restrict__ bin_count,
+                             const int* __restrict__ start, int* __restrict__ rep_cursor, unsigned* __restrict__ crowd) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+    int run = start[b];
+    if (bin_count[b] <= kCrowded) {
+      rep_cursor[b] = run;
+      continue;
+    }
+    atomicOr(&crowd[b >> 5], 1u << (b & 31));
+    for (int r = 0; r < nrep; ++r) {
+      const int c = rep_count[(size_t)r * nbins + b];
+      rep_cursor[(size_t)r * nbins + b] = run;
+      run += c;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ y,
-                          const T* __restrict__ z, Geom g0, FoldConst fc0, int* __restrict__ cursor,
+                          const T* __restrict__ z, Geom g0, FoldConst fc0, int* __restrict__ rep_cursor, int nrep,
+                          int nbins, const unsigned* __restrict__ crowd, int mask_in_smem,
                           typename Traits<T>::Rec* __restrict__ rec, BatchTable bt) {
+  // the crowded-bin mask, staged in shared memory when it fits
+  extern __shared__ unsigned s_crowd[];
+  const int nwords = (nbins + 31) >> 5;
+  if (nrep > 1 && mask_in_smem) {
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) s_crowd[i] = crowd[i];
+    __syncthreads();
+  }
+  const unsigned* mask = mask_in_smem ? s_crowd : crowd;
   const int stride = gridDim.x * blockDim.x;
   for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += kILP * stride) {
     T v[kILP][3];
@@ -344,7 +391,10 @@ __global__ void k_scatter(int M, const T* __restrict__ x, const T* __restrict__ 
           }
         }
         r[u].idx = j;
-        dest[u] = atomicAdd(&cursor[boff + bin_id(g, bb[0], bb[1], bb[2])], 1);  // order inside a bin is arbitrary
+        // order inside a bin is arbitrary
+        const int bin = boff + bin_id(g, bb[0], bb[1], bb[2]);
+        const int rr = (nrep > 1 && ((mask[bin >> 5] >> (bin & 31)) & 1u)) ? (j & (nrep - 1)) : 0;
+        dest[u] = atomicAdd(&rep_cursor[(size_t)rr * nbins + bin], 1);
       }
     }
 #pragma unroll
@@ -399,15 +449,22 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
                      const void* z, int chk, int* bin_count, int* bin_start, int* sub_first,
                      int* cursor, void* rec, int* sub_bin, int* sub_pt0, int* sub_cnt, int* nsub,
                      int* nsparse, int* err, cudaStream_t st, cudaEvent_t* ev, const BatchTable& bt,
-                     int nbins) {
+                     int nbins, const Replicas& rp) {
   const T* xp = (const T*)x;
   const T* yp = g.d > 1 ? (const T*)y : xp;
   const T* zp = g.d > 2 ? (const T*)z : xp;
+  const int nrep = rp.nrep > 1 ? rp.nrep : 1;
+  int* rep_count = nrep > 1 ? rp.count : bin_count;
+  int* rep_cursor = nrep > 1 ? rp.cursor : cursor;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], st);
-  if ((e = cudaMemsetAsync(bin_count, 0, sizeof(int) * (size_t)nbins, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(rep_count, 0, sizeof(int) * (size_t)nbins * nrep, st)) != cudaSuccess) return e;
   if (M > 0) {
-    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, bin_count, err, bt);
+    k_fold_count<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, chk, rep_count, nrep, nbins, err, bt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (nrep > 1) {
+    k_rep_sum<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, nrep, rep_count, bin_count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[1], st);
@@ -418,9 +475,19 @@ cudaError_t setpts_t(const Geom& g, const FoldConst& fc, int M, const void* x, c
                                                    nsparse, sub_bin, sub_pt0, sub_cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], st);
+  // sub_first is free once k_sublist has run: it holds the crowded-bin mask
+  unsigned* crowd = reinterpret_cast<unsigned*>(sub_first);
+  const size_t mask_bytes = sizeof(unsigned) * (size_t)((nbins + 31) / 32);
+  const bool mask_smem = nrep > 1 && mask_bytes <= 32 * 1024;
+  if (nrep > 1) {
+    if ((e = cudaMemsetAsync(crowd, 0, mask_bytes, st)) != cudaSuccess) return e;
+    k_rep_cursor<<<grid_for(nbins, 256), 256, 0, st>>>(nbins, nrep, rep_count, bin_count, bin_start, rep_cursor,
+                                                        crowd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (M > 0) {
-    k_scatter<T><<<grid_for(M, 256), 256, 0, st>>>(M, xp, yp, zp, g, fc, cursor,
-                                                    (typename Traits<T>::Rec*)rec, bt);
+    k_scatter<T><<<grid_for(M, 256), 256, mask_smem ? mask_bytes : 0, st>>>(
+        M, xp, yp, zp, g, fc, rep_cursor, nrep, nbins, crowd, mask_smem ? 1 : 0, (typename Traits<T>::Rec*)rec, bt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[3], st);
@@ -433,13 +500,13 @@ cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t 
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
                           int* sub_first, int* cursor, void* rec, int* sub_bin,
                           int* sub_pt0, int* sub_cnt, int* nsub, int* nsparse, int* err, cudaStream_t st,
-                          cudaEvent_t* ev, const BatchTable& bt, int nbins) {
+                          cudaEvent_t* ev, const BatchTable& bt, int nbins, const Replicas& rp) {
   if (nbins <= 0) nbins = g.nbins;
   if (dbl)
     return setpts_t<double>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
-                            rec, sub_bin, sub_pt0, sub_cnt, nsub, nsparse, err, st, ev, bt, nbins);
+                            rec, sub_bin, sub_pt0, sub_cnt, nsub, nsparse, err, st, ev, bt, nbins, rp);
   return setpts_t<float>(g, fc, (int)M, x, y, z, chkbnds, bin_count, bin_start, sub_first, cursor,
-                         rec, sub_bin, sub_pt0, sub_cnt, nsub, nsparse, err, st, ev, bt, nbins);
+                         rec, sub_bin, sub_pt0, sub_cnt, nsub, nsparse, err, st, ev, bt, nbins, rp);
 }
 
 }  // namespace nufft

@@ -147,6 +147,21 @@ struct FoldConst {  // n / (2 pi) per dimension split into a hi and lo part
 };
 FoldConst make_fold_const(const Geom& g);
 
+// Replicated bin counters / scatter cursors (nrep a power of two; nrep <= 1:
+// none, bin_count and cursor are used directly).  count and cursor hold
+// nrep * nbins ints, replica-major.
+struct Replicas {
+  int nrep;
+  int* count;
+  int* cursor;
+};
+// replicas for nbins bins: up to 32, at most about 4M counters in all
+inline int replicas_for(long long nbins) {
+  int r = 32;
+  while (r > 1 && (long long)r * nbins > (4LL << 20)) r >>= 1;
+  return r;
+}
+
 // Enqueue the whole setpts pipeline.  Work arrays are owned by the plan.
 cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t M, const void* x,
                           const void* y, const void* z, int chkbnds, int* bin_count, int* bin_start,
@@ -154,7 +169,8 @@ cudaError_t launch_setpts(bool dbl, const Geom& g, const FoldConst& fc, int64_t 
                           int* sub_cnt, int* nsub, int* nsparse, int* err, cudaStream_t st,
                           cudaEvent_t* ev /* 4 events or nullptr */,
                           const BatchTable& bt = BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0},
-                          int nbins = 0 /* bin ids over all transforms; 0: g.nbins */);
+                          int nbins = 0 /* bin ids over all transforms; 0: g.nbins */,
+                          const Replicas& rp = Replicas{1, nullptr, nullptr});
 
 // --- spread / interp (spread_interp_*.cu) --------------------------------------
 struct LaunchCfg {

@@ -39,7 +39,9 @@ struct nufft_plan_s {
   int* bin_count = nullptr;
   int* bin_start = nullptr;
   int* sub_first = nullptr;
-  int* cursor = nullptr;  // per-bin scatter cursors
+  int* cursor = nullptr;  // scatter cursors, nrep * nbins (replica-major)
+  int* rep_count = nullptr;  // replicated bin counters, nrep * nbins (nrep > 1)
+  int nrep = 1;
   int* small = nullptr;  // [0] error word, [1] tiled subproblems, [2] work counter, [3] sparse subproblems
   int64_t M = -1;
   int64_t Mcap = 0;
@@ -422,7 +424,8 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   if (dev_alloc(&p->bin_count, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
       dev_alloc(&p->bin_start, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
       dev_alloc(&p->sub_first, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
-      dev_alloc(&p->cursor, sizeof(int) * (size_t)g.nbins) != cudaSuccess ||
+      dev_alloc(&p->cursor, sizeof(int) * (size_t)g.nbins * (size_t)(p->nrep = replicas_for(g.nbins))) != cudaSuccess ||
+      dev_alloc(&p->rep_count, sizeof(int) * (size_t)g.nbins * (size_t)p->nrep) != cudaSuccess ||
       dev_alloc(&p->small, sizeof(int) * 4) != cudaSuccess)
     return fail(p, NUFFT_ERR_ALLOC);
   if (cudaMemset(p->small, 0, sizeof(int) * 4) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
@@ -480,7 +483,8 @@ int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const vo
   cudaError_t e = launch_setpts(p->dbl, g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
                                 p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0,
                                 p->sub_cnt, p->small + 1, p->small + 3, p->small + 0, p->stream,
-                                p->ev_ok ? p->ev : nullptr);
+                                p->ev_ok ? p->ev : nullptr, BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0},
+                                g.nbins, Replicas{p->nrep, p->rep_count, p->cursor});
   if (e != cudaSuccess) return NUFFT_ERR_CUDA;
   p->M = M;
   p->last_steps = 1;
@@ -630,7 +634,7 @@ int plan_reserve(nufft_plan p, int64_t mcap) {
 size_t plan_device_bytes(nufft_plan p) {
   if (!p) return 0;
   size_t rs = p->dbl ? 8 : 4, cs = p->csize;
-  size_t b = (size_t)p->ngrid * cs + 4 * sizeof(int) * (size_t)p->g.nbins + 4 * sizeof(int);
+  size_t b = (size_t)p->ngrid * cs + (3 + 2 * (size_t)p->nrep) * sizeof(int) * (size_t)p->g.nbins + 4 * sizeof(int);
   for (int i = 0; i < 3; ++i) b += (size_t)p->N[i] * rs;
   b += (size_t)p->Mcap * (p->dbl ? sizeof(RecD) : sizeof(RecF)) + 3 * sizeof(int) * (size_t)p->subcap;
   size_t ws = 0;
@@ -661,7 +665,7 @@ int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, in
   choose_bins(g, dbl, o);
   size_t cs = dbl ? 16 : 8, rs = dbl ? 8 : 4;
   size_t ngrid = (size_t)n[0] * (size_t)n[1] * (size_t)n[2];
-  size_t b = 2 * ngrid * cs + 4 * sizeof(int) * (size_t)g.nbins + 4 * sizeof(int);
+  size_t b = 2 * ngrid * cs + (3 + 2 * (size_t)replicas_for(g.nbins)) * sizeof(int) * (size_t)g.nbins + 4 * sizeof(int);
   for (int i = 0; i < dim; ++i) b += (size_t)nmodes[i] * rs;
   int64_t subcap = std::min<int64_t>(g.nbins, mcap) + mcap / g.maxsub + 1;
   b += (size_t)mcap * (dbl ? sizeof(RecD) : sizeof(RecF)) + 3 * sizeof(int) * (size_t)subcap;
@@ -694,7 +698,7 @@ int nufft_destroy(nufft_plan p) {
   if (p->ev_ok)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(p->ev[i]);
   void* bufs[] = {p->grid, p->pk[0], p->pk[1], p->pk[2], p->bin_count, p->bin_start, p->sub_first,
-                  p->cursor, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
+                  p->cursor, p->rep_count, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
   for (void* b : bufs)
     if (b) cudaFree(b);
   cudaSetDevice(dev);
@@ -789,7 +793,9 @@ struct nufft_batch_s {
   int* bin_count = nullptr;
   int* bin_start = nullptr;
   int* sub_first = nullptr;
-  int* cursor = nullptr;
+  int* cursor = nullptr;  // nrep * total_bins
+  int* rep_count = nullptr;
+  int nrep = 1;
   int* small = nullptr;  // [0] error word, [1] tiled subproblems, [2] work counter, [3] sparse subproblems
   int64_t M = -1, Mcap = 0, subcap = 0;
   void* rec = nullptr;
@@ -991,7 +997,9 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
       dev_alloc(&p->bin_count, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
       dev_alloc(&p->bin_start, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
       dev_alloc(&p->sub_first, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
-      dev_alloc(&p->cursor, sizeof(int) * (size_t)p->total_bins) != cudaSuccess ||
+      dev_alloc(&p->cursor, sizeof(int) * (size_t)p->total_bins * (size_t)(p->nrep = replicas_for(p->total_bins))) !=
+          cudaSuccess ||
+      dev_alloc(&p->rep_count, sizeof(int) * (size_t)p->total_bins * (size_t)p->nrep) != cudaSuccess ||
       dev_alloc(&p->small, sizeof(int) * 4) != cudaSuccess)
     return batch_fail(p, NUFFT_ERR_ALLOC);
   bool okc = true;
@@ -1061,7 +1069,8 @@ int nufft_batch_setpts(nufft_batch p, const int64_t* offsets, const void* x, con
   FoldConst fc = make_fold_const(p->g);
   cudaError_t e = launch_setpts(p->dbl, p->g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
                                 p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1,
-                                p->small + 3, p->small + 0, p->stream, nullptr, table_of(p), p->total_bins);
+                                p->small + 3, p->small + 0, p->stream, nullptr, table_of(p), p->total_bins,
+                                Replicas{p->nrep, p->rep_count, p->cursor});
   if (e != cudaSuccess) return NUFFT_ERR_CUDA;
   p->M = M;
   return NUFFT_OK;
@@ -1109,7 +1118,7 @@ int nufft_batch_destroy(nufft_batch p) {
   for (auto& c : p->classes)
     if (c.ok) cufftDestroy(c.plan);
   void* bufs[] = {p->grid, p->pk, p->bg, p->boff, p->poff, p->growoff, p->mrowoff, p->bin_count, p->bin_start,
-                  p->sub_first, p->cursor, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
+                  p->sub_first, p->cursor, p->rep_count, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
   for (void* b : bufs)
     if (b) cudaFree(b);
   cudaSetDevice(dev);
