@@ -40,7 +40,7 @@ METRIC = "type1/2 NU points/s at eps=1e-5 (3D, fp32)"
 # valid only for the kernel source they were measured on.
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1808_06736_gb300", "csrc", "spread_interp.cuh")
 MEASURED_TRAFFIC = {
-    "sha256": "e298ab24f44a9877bf086825166be35d82acc9918a75ef0708a6e1527fbc42cf",
+    "sha256": "4e42bd3250a97faacc77fa0758c17ec398bba237e10c0d16591c80ae26ab243c",
     "spread": 15070201600 + 1226339072,
     "interp": 6020471040 + 3177263104,
 }
@@ -48,7 +48,8 @@ MEASURED_TRAFFIC = {
 
 def measured_traffic(kernel: str, args) -> int | None:
     import hashlib
-    default = (args.M == 100_000_000 and args.N == 256 and args.eps == 1e-5 and args.kind == "uniform")
+    default = (args.M == 100_000_000 and args.N == 256 and args.eps == 1e-5 and args.kind == "uniform" and
+               args.prec == "c64")
     try:
         digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
     except OSError:
@@ -58,6 +59,7 @@ def measured_traffic(kernel: str, args) -> int | None:
     return MEASURED_TRAFFIC.get(kernel)
 UNIT = "NU points/s"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
 
 
 def parse():
@@ -70,6 +72,8 @@ def parse():
     ap.add_argument("--N", type=int, default=256)
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--kind", default="uniform", choices=["uniform", "clustered"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"],
+                    help="c64 (the headline: complex64, float arithmetic) or c128 (complex128, double)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=300_000)
@@ -183,14 +187,16 @@ def run_cuda(args, ws, rank, local):
     d, N, M, eps = 3, args.N, args.M, args.eps
     Ns = [N] * d
     seed = 1000 + 2 + 10 * (1 if args.kind == "clustered" else 0) + rank
-    xs = I.torch_points(seed, M, d, args.kind, dev, torch.float32)
-    c = I.torch_complex_normal(seed + 1, M, dev, torch.complex64)
-    f = I.torch_complex_normal(seed + 2, N ** d, dev, torch.complex64)
+    cdt = torch.complex128 if args.prec == "c128" else torch.complex64
+    rdt = torch.float64 if args.prec == "c128" else torch.float32
+    xs = I.torch_points(seed, M, d, args.kind, dev, rdt)
+    c = I.torch_complex_normal(seed + 1, M, dev, cdt)
+    f = I.torch_complex_normal(seed + 2, N ** d, dev, cdt)
     stream = torch.cuda.current_stream(dev)
-    p1 = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=torch.complex64, device=dev, debug=1)
-    p2 = pkg.Plan(2, Ns, eps=eps, isign=-1, dtype=torch.complex64, device=dev, debug=1)
-    fout = torch.empty((1,) + tuple(Ns), dtype=torch.complex64, device=dev)
-    cout = torch.empty((1, M), dtype=torch.complex64, device=dev)
+    p1 = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=cdt, device=dev, debug=1)
+    p2 = pkg.Plan(2, Ns, eps=eps, isign=-1, dtype=cdt, device=dev, debug=1)
+    fout = torch.empty((1,) + tuple(Ns), dtype=cdt, device=dev)
+    cout = torch.empty((1, M), dtype=cdt, device=dev)
     slots = {k: [] for k in ("fold", "scan", "scatter", "spread", "fft1", "deconv", "precorrect", "fft2",
                              "interp")}
 
@@ -255,8 +261,8 @@ def run_cuda(args, ws, rank, local):
         df = [torch.empty_like(f) for _ in range(nb)]
         dfo = [torch.empty_like(fout) for _ in range(nb)]
         dco = [torch.empty_like(cout) for _ in range(nb)]
-        hfo = [torch.empty(fout.shape, dtype=torch.complex64).pin_memory() for _ in range(nb)]
-        hco = [torch.empty(cout.shape, dtype=torch.complex64).pin_memory() for _ in range(nb)]
+        hfo = [torch.empty(fout.shape, dtype=cdt).pin_memory() for _ in range(nb)]
+        hco = [torch.empty(cout.shape, dtype=cdt).pin_memory() for _ in range(nb)]
         up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         inputs_free = [torch.cuda.Event() for _ in range(nb)]
         outputs_free = [torch.cuda.Event() for _ in range(nb)]
@@ -302,8 +308,9 @@ def run_cuda(args, ws, rank, local):
         e1.record(stream)
         barrier()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / ke, dev)
-        h2d = sum(v.numel() * v.element_size() for v in hx) + hc.numel() * 8 + hf.numel() * 8
-        d2h = hfo[0].numel() * 8 + hco[0].numel() * 8
+        h2d = sum(v.numel() * v.element_size() for v in hx) + hc.numel() * hc.element_size() + \
+            hf.numel() * hf.element_size()
+        d2h = hfo[0].numel() * hfo[0].element_size() + hco[0].numel() * hco[0].element_size()
         e2e = {"value": aggregate_value(2 * M, ms_e2e, ws), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "pipelining": "uploads and downloads on their own streams, double buffered"}
@@ -316,15 +323,23 @@ def run_cuda(args, ws, rank, local):
     achieved = flops / (med[dominant] * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12  # max SM clock 2070 MHz
-    roof = {"bound": "alu", "kernel": "k_%s (3D, w=%d, fp32)" % (dominant, w), "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": measured_traffic(dominant, args),
-            "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop x 2.07 GHz" % (sms, FP32_LANES_PER_SM),
+    if args.prec == "c64":
+        peak = sms * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12  # max SM clock 2070 MHz
+        src = "derived: %d SMs x %d FP32 lanes x 2 flop x 2.07 GHz" % (sms, FP32_LANES_PER_SM)
+    else:
+        peak = FP64_NOMINAL_TFLOPS
+        src = "nominal FP64 rate of the GB300 (no measured FP64 peak is provided)"
+    roof = {"bound": "alu", "kernel": "k_%s (3D, w=%d, %s)" % (dominant, w, "fp32" if args.prec == "c64" else "fp64"),
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": measured_traffic(dominant, args), "peak_source": src,
             "algorithmic_flops_per_point": algorithmic_units(d, w)}
     kernels_ms = {k: round(v, 4) for k, v in med.items()}
     p1.close()
     p2.close()
-    launches = args.steps * 12  # per step: 4 setpts kernels x 2 plans + spread, deconv, precorrect, interp
+    # per step: 6 setpts kernels (fold, replica sum, scan, subproblem list, replica
+    # cursors, scatter) x 2 plans + tiled and per-warp spread, deconvolve,
+    # pre-correct scatter, tiled and per-warp interp (cuFFT's kernels not counted)
+    launches = args.steps * 18
     return {"value": value, "ms": ms_max, "e2e": e2e, "roofline": roof, "kernels_ms": kernels_ms,
             "clocks": clk, "gpu_launches": launches, "w": w}
 
@@ -651,8 +666,9 @@ def run_serving_line(args):
 
 
 def config_dict(args):
-    return {"workload": "3D type 1 + type 2, N=%d^3 modes (fine grid %d^3), M=%d %s points, complex64, eps=%g"
-                        % (args.N, 2 * args.N, args.M, args.kind, args.eps),
+    return {"workload": "3D type 1 + type 2, N=%d^3 modes (fine grid %d^3), M=%d %s points, %s, eps=%g"
+                        % (args.N, 2 * args.N, args.M, args.kind,
+                           "complex64" if args.prec == "c64" else "complex128", args.eps),
             "modes": [args.N] * 3, "fine_grid": [2 * args.N] * 3, "M": args.M, "points": args.kind,
             "eps": args.eps, "step": "setpts+type1 and setpts+type2 on the same points; value = 2M/step",
             "l2": "inputs larger than L2 (1.2 GB coordinates, 1 GB fine grids), no flush",
@@ -681,9 +697,11 @@ def main():
                "sample": "spread+interp on %d of %d points (%.2f s, scaled linearly in M), FFT+correction on "
                          "the full grid (%.2f s, scipy FFT on %d threads; C loops single-threaded)"
                          % (args.cpu_sample, args.M, t_pts, t_fixed, cores)}
-    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    metric = METRIC if args.prec == "c64" else "type1/2 NU points/s at eps=%g (3D, fp64)" % args.eps
+    line = {"metric": metric, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args),
+            "vs_baseline": None, "dtype": "f32" if args.prec == "c64" else "f64", "data": "synthetic",
+            "config": config_dict(args),
             "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
             "gpu_launches": r["gpu_launches"], "kernels_ms": r["kernels_ms"], "serving": serving}
     print(json.dumps(line))
