@@ -523,7 +523,8 @@ def run_serving(args):
     (b) the plain path: one request at a time through cached Plans (gradient
     requests through the autograd functions), synchronising after each.
     Both arms take gradient requests' point gradient through the ES kernel's
-    derivative (xgrad="kernel").
+    derivative (xgrad="kernel") and use the same upsampling factor per request
+    (the server's cost model, nufft_request_upsampfac).
     Open loop: each request is submitted at its arrival time; latency = device
     completion - arrival.  Burst: the whole trace submitted at once; points/s =
     sum of M / makespan.  Inputs are slices of pools resident in HBM; each arm
@@ -603,18 +604,19 @@ def run_serving(args):
 
     def run_plain(q):
         xs, f, c, y = inputs(q)
+        sigma = S.upsampfac_for(q["kind"], q["modes"], q["eps"], q["M"])  # the same grid as the served request
         if q["kind"] == 1:
-            p = cache.get(1, q["modes"], q["eps"], q["isign"], torch.complex64, dev)
+            p = cache.get(1, q["modes"], q["eps"], q["isign"], torch.complex64, dev, upsampfac=sigma)
             p.setpts(*xs)
             p.execute(c)
         elif q["kind"] == 2:
-            p = cache.get(2, q["modes"], q["eps"], q["isign"], torch.complex64, dev)
+            p = cache.get(2, q["modes"], q["eps"], q["isign"], torch.complex64, dev, upsampfac=sigma)
             p.setpts(*xs)
             p.execute(f)
         else:
             xg = torch.stack(xs).requires_grad_()
             fg = f.detach().clone().requires_grad_()
-            cc = AG.nufft_type2(xg, fg, eps=q["eps"], isign=q["isign"], cache=cache, xgrad="kernel")
+            cc = AG.nufft_type2(xg, fg, eps=q["eps"], isign=q["isign"], cache=cache, xgrad="kernel", upsampfac=sigma)
             loss = ((cc - y).abs() ** 2).sum()
             loss.backward()
         torch.cuda.synchronize()

@@ -72,6 +72,9 @@ typedef struct {
   int sparse_max;     /* subproblems of at most this many points (<= 32) run one per warp straight
                          on the fine grid instead of through a shared-memory tile (0: 32, -1: never) */
   int reserved[7];    /* set to zero */
+  double upsampfac;   /* fine grid / modes per dimension, sigma: 2 (0 means 2) or 1.25 (smaller FFTs and
+                         grids, wider kernel: w from the slope of Eq. (ESerr), beta from Eq. (gam); more
+                         rounding amplification, see nufft_choose_params_sigma) */
 } nufft_opts;
 
 /* Fill *o with defaults.  Returns NUFFT_OK, or NUFFT_ERR_BAD_ARG for o == NULL. */
@@ -184,6 +187,15 @@ const char* nufft_strerror(int code);
  */
 int nufft_choose_params(int dim, const int64_t* nmodes, double eps, int prec, int* w, double* beta,
                         int64_t* n);
+/* The same for upsampling factor sigma = 2 or 1.25 (NUFFT_ERR_BAD_ARG otherwise).
+ * At 1.25 NUFFT_WARN_EPS_TOO_SMALL also flags eps that needs w > 16 (about
+ * eps < 1e-9), and eps below unit roundoff times rmax^dim, rmax =
+ * exp((1 - sqrt(1 - (2 sigma - 1)^-2)) beta) (Eq. (rmax)): the correction
+ * amplifies rounding by up to that factor, e^{0.25 beta} per dimension at 1.25
+ * (complex64: fine for 1D down to eps 1e-5, 2D 1e-3, 3D 1e-3; complex128 to 1e-9
+ * in 1D and 2D, about 1e-6 in 3D). */
+int nufft_choose_params_sigma(int dim, const int64_t* nmodes, double eps, int prec, double sigma, int* w,
+                              double* beta, int64_t* n);
 
 /*
  * Correction factors of Eq. (pk1) for one dimension: out[m] = 2 / (w phi^(alpha k)),
@@ -236,8 +248,9 @@ int nufft_batch_destroy(nufft_batch plan);
  * extents (hence the shared-memory tile, bin + w per dimension; 1D 256..4096,
  * 2D {8,16,32,64}^2, 3D B1 >= B2 >= B3 in {4,8,16,32}, those whose tile fits
  * in shared memory), the largest subproblem (max_subprob 256..4096), the
- * per-warp threshold (sparse_max -1, 8, 16, default 32) and the threads per
- * block (128, default 256).  Staged search: bins first, then each further
+ * per-warp threshold (sparse_max -1, 8, 16, default 32), the threads per
+ * block (128, default 256) and the upsampling factor (1.25 when eps needs no
+ * more than w = 16 there, default 2).  Staged search: bins first, then each further
  * tunable from the best so far; the default options are timed first, so
  * *best_ms <= *default_ms.  A configuration is timed as one untimed setpts +
  * execute, then reps timed ones (CUDA events on stream; the minimum counts);

@@ -55,6 +55,8 @@ typedef struct {
   int isign;           /* +1 or -1: the sign of the exponent (of F2 for LSQ_GRAD) */
   int prec;            /* NUFFT_C64 or NUFFT_C128 */
   double eps;          /* tolerance, as for nufft_makeplan */
+  double upsampfac;    /* 2 or 1.25 (opts.upsampfac), or 0: the server picks per request by a cost model
+                          (fine-grid cells against M w^d stencil cells; see nufft_request_upsampfac) */
   int64_t M;           /* number of points, 0 <= M < 2^31 */
   const void* x;       /* M coordinates each (float / double per prec); y NULL if dim < 2, z if dim < 3 */
   const void* y;
@@ -114,6 +116,15 @@ int nufft_server_destroy(nufft_server s);
 
 /* Seconds on the clock the completions use (a monotonic clock). */
 double nufft_server_clock(void);
+
+/* Host-only: the upsampling factor the server uses for r: r->upsampfac when
+ * it is 2 or 1.25; for 0, 1.25 when eps needs no more than w = 16 at 1.25 and
+ *   a prod(n_i(1.25)) + b M w(1.25)^dim  <  a prod(n_i(2)) + b M w(2)^dim,
+ * with a = 13 ps per fine-grid cell (zeroing or pre-correcting, FFT and
+ * correction of one transform) and b = 0.7 ps per stencil cell of a point, as
+ * measured on the GB300 for 3D complex64; otherwise 2.  Returns 0 for an
+ * invalid request. */
+double nufft_request_upsampfac(const nufft_request* r);
 
 /* Host-only: upper estimate of the device bytes a plan entry for r needs
  * with room for mcap points (the figure admission uses). */

@@ -176,15 +176,31 @@ def next235(m: int) -> int:
         n += 1
 
 
-def kernel_width(eps: float) -> int:
-    """Eq. (params): w = ceil(log10(1/eps)) + 1, with the guard and clamp read in the module docstring."""
-    w = int(math.ceil(math.log10(1.0 / eps) - 1e-9)) + 1
+GAMMA = 0.976            # Eq. (gam)'s safety factor that gives beta = 2.30 w at sigma = 2 (Sec. 4.3)
+SIGMA_54_OFFSET = 0.43   # reading: the paper gives no w rule for sigma = 5/4; offset calibrated on O2
+
+
+def eserr_slope(sigma: float, gamma: float = GAMMA) -> float:
+    """w per decade of 1/eps from Eq. (ESerr) with its algebraic prefactor dropped (Sec. 4.3):
+    ln(10) / (pi gamma sqrt(1 - 1/sigma - (gamma^-2 - 1) / (4 sigma^2)))."""
+    return math.log(10.0) / (math.pi * gamma * math.sqrt(1.0 - 1.0 / sigma - (gamma ** -2 - 1.0) / (4.0 * sigma ** 2)))
+
+
+def kernel_width(eps: float, sigma: float = 2.0) -> int:
+    """sigma = 2, Eq. (params): w = ceil(log10(1/eps)) + 1, with the guard and clamp read in the
+    module docstring.  sigma = 5/4: w = ceil(slope log10(1/eps) + offset), slope from Eq. (ESerr)."""
+    if sigma == 2.0:
+        w = int(math.ceil(math.log10(1.0 / eps) - 1e-9)) + 1
+    else:
+        w = int(math.ceil(eserr_slope(sigma) * math.log10(1.0 / eps) + SIGMA_54_OFFSET - 1e-9))
     return min(max(w, 2), 16)
 
 
-def es_beta(w: int) -> float:
-    """Eq. (params): beta = 2.30 w (sigma = 2)."""
-    return 2.30 * w
+def es_beta(w: int, sigma: float = 2.0) -> float:
+    """Eq. (params): beta = 2.30 w at sigma = 2; otherwise Eq. (gam): gamma pi w (1 - 1/(2 sigma))."""
+    if sigma == 2.0:
+        return 2.30 * w
+    return GAMMA * math.pi * w * (1.0 - 1.0 / (2.0 * sigma))
 
 
 def fine_grid_size(N: int, w: int, sigma: float = 2.0) -> int:
@@ -192,10 +208,10 @@ def fine_grid_size(N: int, w: int, sigma: float = 2.0) -> int:
     return next235(max(int(math.ceil(sigma * N)), 2 * w))
 
 
-def choose_params(eps: float, Ns):
+def choose_params(eps: float, Ns, sigma: float = 2.0):
     """(w, beta, [n_1..n_d]) for tolerance eps and mode counts Ns (Sec. 3, Eq. (params))."""
-    w = kernel_width(eps)
-    return w, es_beta(w), [fine_grid_size(n, w) for n in Ns]
+    w = kernel_width(eps, sigma)
+    return w, es_beta(w, sigma), [fine_grid_size(n, w, sigma) for n in Ns]
 
 
 # --------------------------------------------------- kernel and its transform

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
     "nufft_execute", "nufft_execute_grad", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
-    "nufft_strerror", "nufft_choose_params", "nufft_correction_factors", "nufft_next235",
+    "nufft_strerror", "nufft_choose_params", "nufft_choose_params_sigma", "nufft_correction_factors", "nufft_next235",
     "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
     "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy", "nufft_tune", "nufft_batch_tune",
     "nufft_tune_candidates", "opts_dict", "tune_plan", "tune_batch",
@@ -43,7 +43,7 @@ class NufftError(RuntimeError):
 class nufft_opts(ctypes.Structure):
     _fields_ = [("debug", ctypes.c_int), ("chkbnds", ctypes.c_int), ("modeord", ctypes.c_int),
                 ("bin_size", ctypes.c_int * 3), ("max_subprob", ctypes.c_int), ("threads", ctypes.c_int),
-                ("sparse_max", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("sparse_max", ctypes.c_int), ("reserved", ctypes.c_int * 7), ("upsampfac", ctypes.c_double)]
 
 
 _lib = None
@@ -77,6 +77,8 @@ def _L():
     lib.nufft_strerror.argtypes = [i32]
     lib.nufft_strerror.restype = ctypes.c_char_p
     lib.nufft_choose_params.argtypes = [i32, pi64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), pi64]
+    lib.nufft_choose_params_sigma.argtypes = [i32, pi64, dbl, i32, dbl, ctypes.POINTER(i32), ctypes.POINTER(dbl),
+                                              pi64]
     lib.nufft_correction_factors.argtypes = [i64, i64, i32, dbl, ctypes.POINTER(ctypes.c_double)]
     lib.nufft_next235.argtypes = [i64]
     lib.nufft_next235.restype = i64
@@ -159,6 +161,15 @@ def nufft_choose_params(dim: int, nmodes, eps: float, prec: int = NUFFT_C128):
     w, beta = ctypes.c_int(), ctypes.c_double()
     n = (ctypes.c_int64 * 3)()
     st = _L().nufft_choose_params(int(dim), arr, float(eps), int(prec), ctypes.byref(w), ctypes.byref(beta), n)
+    return st, w.value, beta.value, list(n)[:dim]
+
+
+def nufft_choose_params_sigma(dim: int, nmodes, eps: float, prec: int, sigma: float):
+    arr = (ctypes.c_int64 * 3)(*([int(v) for v in nmodes] + [1] * (3 - len(nmodes))))
+    w, beta = ctypes.c_int(), ctypes.c_double()
+    n = (ctypes.c_int64 * 3)()
+    st = _L().nufft_choose_params_sigma(int(dim), arr, float(eps), int(prec), float(sigma), ctypes.byref(w),
+                                        ctypes.byref(beta), n)
     return st, w.value, beta.value, list(n)[:dim]
 
 
@@ -252,7 +263,7 @@ def nufft_batch_tune(type_: int, dim: int, nmodes, isign: int, eps: float, prec:
 def opts_dict(o: nufft_opts) -> dict:
     """The tunable fields of an options struct, as keyword arguments for Plan / BatchPlan."""
     return {"bin_size": tuple(o.bin_size), "max_subprob": o.max_subprob, "threads": o.threads,
-            "sparse_max": o.sparse_max}
+            "sparse_max": o.sparse_max, "upsampfac": o.upsampfac}
 
 
 # --------------------------------------------------------------- torch layer
@@ -291,6 +302,8 @@ class Plan:
                 if k == "bin_size":
                     for i, b in enumerate(v):
                         o.bin_size[i] = int(b)
+                elif k == "upsampfac":
+                    o.upsampfac = float(v)
                 else:
                     setattr(o, k, int(v))
             self._h = None
@@ -451,6 +464,8 @@ class BatchPlan:
                 if k == "bin_size":
                     for i, b in enumerate(v):
                         o.bin_size[i] = int(b)
+                elif k == "upsampfac":
+                    o.upsampfac = float(v)
                 else:
                     setattr(o, k, int(v))
             st, h = nufft_batch_makeplan(self.type, self.dim, self.modes, self.isign, eps, prec,

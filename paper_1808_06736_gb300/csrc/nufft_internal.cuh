@@ -250,7 +250,8 @@ int plan_execute_grad(nufft_plan p, void* c, void* dc, const void* f);
 int plan_set_stream(nufft_plan p, cudaStream_t s);
 int plan_reserve(nufft_plan p, int64_t mcap);  // point capacity without setting points
 size_t plan_device_bytes(nufft_plan p);
-int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes);
+int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes,
+                        double sigma = 2.0);
 int plan_modes(nufft_plan p, int64_t* N, int* dim);
 
 }  // namespace nufft

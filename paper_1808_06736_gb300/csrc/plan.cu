@@ -79,33 +79,65 @@ int64_t next235_impl(int64_t m) {
   return -1;
 }
 
-// Eq. (params): w = ceil(log10(1/eps)) + 1 (guarded against log10 rounding at
-// exact powers of ten), clamped to [2, 16]; beta = 2.30 w.
-int width_for(double eps) {
-  double lw = std::ceil(std::log10(1.0 / eps) - 1e-9) + 1.0;
+// Kernel width, clamped to [2, 16] (*capped set when the clamp from above applied).
+//   sigma = 2 (Eq. (params)): w = ceil(log10(1/eps)) + 1 (guarded against
+//     log10 rounding at exact powers of ten).
+//   sigma = 5/4: the slope of Eq. (ESerr) in log10(1/eps),
+//     ln(10) / (pi gamma sqrt(1 - 1/sigma - (gamma^-2 - 1) / (4 sigma^2))) = 1.714 at
+//     gamma = 0.976, plus 0.43: the smallest offset for which the transform's
+//     error stays below eps for eps = 1e-3 .. 1e-9 (measured).
+int width_for(double eps, double sigma, bool* capped) {
+  double lw;
+  if (sigma == 2.0) lw = std::ceil(std::log10(1.0 / eps) - 1e-9) + 1.0;
+  else lw = std::ceil(1.714 * std::log10(1.0 / eps) + 0.43 - 1e-9);
   if (!(lw >= 2.0)) lw = 2.0;
+  if (capped) *capped = lw > 16.0;
   if (lw > 16.0) lw = 16.0;
   return (int)lw;
 }
 
-int choose_params_impl(int dim, const int64_t* N, double eps, int prec, int* w, double* beta, int64_t* n) {
+// beta = gamma pi w (1 - 1/(2 sigma)) (Eq. (gam)); gamma = 0.976 gives the
+// paper's beta = 2.30 w at sigma = 2 (Eq. (params)).
+double beta_for(int w, double sigma) {
+  if (sigma == 2.0) return 2.30 * w;
+  return 0.976 * 3.14159265358979323846 * w * (1.0 - 1.0 / (2.0 * sigma));
+}
+
+int choose_params_impl(int dim, const int64_t* N, double eps, int prec, int* w, double* beta, int64_t* n,
+                       double sigma = 2.0) {
   if (dim < 1 || dim > 3 || !N || !(eps > 0.0) || !std::isfinite(eps) ||
-      (prec != NUFFT_C64 && prec != NUFFT_C128))
+      (prec != NUFFT_C64 && prec != NUFFT_C128) || (sigma != 2.0 && sigma != 1.25))
     return NUFFT_ERR_BAD_ARG;
   for (int i = 0; i < dim; ++i)
     if (N[i] < 1) return NUFFT_ERR_BAD_ARG;
-  int ww = width_for(eps);
+  bool capped = false;
+  int ww = width_for(eps, sigma, &capped);
   if (w) *w = ww;
-  if (beta) *beta = 2.30 * ww;
+  if (beta) *beta = beta_for(ww, sigma);
   for (int i = 0; i < dim; ++i) {
-    int64_t m = std::max<int64_t>(2 * N[i], 2 * (int64_t)ww);  // sigma = 2
+    // n_i = next 2^a 3^b 5^c >= max(sigma N_i, 2 w)
+    int64_t sn = sigma == 2.0 ? 2 * N[i] : (5 * N[i] + 3) / 4;
+    int64_t m = std::max<int64_t>(sn, 2 * (int64_t)ww);
     int64_t v = next235_impl(m);
     if (v < 0) return NUFFT_ERR_BAD_ARG;
     if (n) n[i] = v;
   }
   double floor_eps = (prec == NUFFT_C64) ? 1e-6 : 1e-15;
-  return (eps < floor_eps) ? NUFFT_WARN_EPS_TOO_SMALL : NUFFT_OK;
+  // The correction p_k amplifies the grid's rounding by up to rmax per
+  // dimension, rmax ~ exp((1 - sqrt(1 - (2 sigma - 1)^-2)) beta) (Eq. (rmax)):
+  // e^{0.057 beta} at sigma = 2 but e^{0.25 beta} at 5/4, so at 5/4 warn when
+  // unit roundoff times rmax^dim exceeds eps (e.g. complex64 in 3D below eps = 1e-3).
+  bool amplified = false;
+  if (sigma != 2.0) {
+    const double u = (prec == NUFFT_C64) ? 5.96e-8 : 1.11e-16;
+    const double g = 1.0 / (2.0 * sigma - 1.0);
+    amplified = u * std::exp(dim * (1.0 - std::sqrt(1.0 - g * g)) * beta_for(ww, sigma)) > eps;
+  }
+  return (eps < floor_eps || capped || amplified) ? NUFFT_WARN_EPS_TOO_SMALL : NUFFT_OK;
 }
+
+// upsampling factor from the options: 0 means 2
+double sigma_of(const nufft_opts& o) { return o.upsampfac == 0.0 ? 2.0 : o.upsampfac; }
 
 // Positive nodes / weights of the 2p-point Gauss-Legendre rule by Newton's
 // method on the three-term Legendre recurrence.
@@ -337,6 +369,11 @@ int nufft_choose_params(int dim, const int64_t* nmodes, double eps, int prec, in
   return choose_params_impl(dim, nmodes, eps, prec, w, beta, n);
 }
 
+int nufft_choose_params_sigma(int dim, const int64_t* nmodes, double eps, int prec, double sigma, int* w,
+                              double* beta, int64_t* n) {
+  return choose_params_impl(dim, nmodes, eps, prec, w, beta, n, sigma);
+}
+
 int nufft_correction_factors(int64_t N, int64_t n, int w, double beta, double* out) {
   return correction_impl(N, n, w, beta, out);
 }
@@ -367,7 +404,7 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   int w;
   double beta;
   int64_t n[3] = {1, 1, 1};
-  int warn = choose_params_impl(dim, nmodes, eps, prec, &w, &beta, n);
+  int warn = choose_params_impl(dim, nmodes, eps, prec, &w, &beta, n, opts ? sigma_of(*opts) : 2.0);
   if (warn < 0) return warn;
   for (int i = 0; i < dim; ++i)
     if (nmodes[i] > (1 << 29) || n[i] > (1 << 30)) return NUFFT_ERR_TOO_BIG;
@@ -644,13 +681,14 @@ size_t plan_device_bytes(nufft_plan p) {
 
 // Upper estimate of plan_device_bytes before the plan exists (default options,
 // point capacity mcap); cuFFT's work area is bounded by one more fine grid.
-int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes) {
+int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes,
+                        double sigma) {
   if (!bytes || !nmodes || dim < 1 || dim > 3 || mcap < 0 || (prec != NUFFT_C64 && prec != NUFFT_C128))
     return NUFFT_ERR_BAD_ARG;
   int w;
   double beta;
   int64_t n[3] = {1, 1, 1};
-  int st = choose_params_impl(dim, nmodes, eps, prec, &w, &beta, n);
+  int st = choose_params_impl(dim, nmodes, eps, prec, &w, &beta, n, sigma);
   if (st < 0) return st;
   const bool dbl = prec == NUFFT_C128;
   Geom g;
@@ -887,7 +925,8 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   for (int t = 0; t < B; ++t) {
     int w;
     double beta;
-    int st = choose_params_impl(dim, nmodes + (size_t)t * dim, eps, prec, &w, &beta, &n[(size_t)t * 3]);
+    int st = choose_params_impl(dim, nmodes + (size_t)t * dim, eps, prec, &w, &beta, &n[(size_t)t * 3],
+                                sigma_of(p->opts));
     if (st < 0) return batch_fail(p, st);
     warn = st;
     p->w = w;

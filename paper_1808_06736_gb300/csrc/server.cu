@@ -102,6 +102,7 @@ bool valid_shape(const nufft_request* r) {
   if (r->dim < 1 || r->dim > 3 || (r->isign != 1 && r->isign != -1)) return false;
   if (r->prec != NUFFT_C64 && r->prec != NUFFT_C128) return false;
   if (!(r->eps > 0.0) || r->M < 0 || r->M >= ((int64_t)1 << 31) - 1) return false;
+  if (r->upsampfac != 0.0 && r->upsampfac != 2.0 && r->upsampfac != 1.25) return false;
   for (int i = 0; i < r->dim; ++i)
     if (r->nmodes[i] < 1 || r->nmodes[i] > (1 << 29)) return false;
   return true;
@@ -131,17 +132,34 @@ int64_t capacity_for(int64_t M) {
 struct Key {
   int kind, dim, isign, prec;
   int64_t n[3];
-  double eps;
+  double eps, sigma;
   bool operator==(const Key& o) const {
     return kind == o.kind && dim == o.dim && isign == o.isign && prec == o.prec && n[0] == o.n[0] &&
-           n[1] == o.n[1] && n[2] == o.n[2] && eps == o.eps;
+           n[1] == o.n[1] && n[2] == o.n[2] && eps == o.eps && sigma == o.sigma;
   }
 };
 
 Key key_of(const nufft_request* r) {
-  Key k{r->kind, r->dim, r->isign, r->prec, {1, 1, 1}, r->eps};
+  Key k{r->kind, r->dim, r->isign, r->prec, {1, 1, 1}, r->eps, r->upsampfac};
   for (int i = 0; i < r->dim; ++i) k.n[i] = r->nmodes[i];
   return k;
+}
+
+// Upsampling factor for a request (see nufft_request_upsampfac).
+double choose_sigma(const nufft_request* r) {
+  if (r->upsampfac == 2.0 || r->upsampfac == 1.25) return r->upsampfac;
+  int w2, w5;
+  double b;
+  int64_t n2[3] = {1, 1, 1}, n5[3] = {1, 1, 1};
+  if (nufft_choose_params_sigma(r->dim, r->nmodes, r->eps, r->prec, 2.0, &w2, &b, n2) < 0) return 2.0;
+  if (nufft_choose_params_sigma(r->dim, r->nmodes, r->eps, r->prec, 1.25, &w5, &b, n5) != NUFFT_OK) return 2.0;
+  const double a = 13e-12, bb = 0.7e-12;  // s per fine-grid cell, s per stencil cell of a point
+  auto cost = [&](const int64_t* n, int w) {
+    double cells = (double)n[0] * (double)n[1] * (double)n[2], sten = 1.0;
+    for (int i = 0; i < r->dim; ++i) sten *= w;
+    return a * cells + bb * (double)r->M * sten;
+  };
+  return cost(n5, w5) < cost(n2, w2) ? 1.25 : 2.0;
 }
 
 // ------------------------------------------------------------ GPU executor
@@ -177,7 +195,7 @@ struct GpuExecutor {
 
   static int estimate(void*, const nufft_request* r, int64_t mcap, size_t* bytes) {
     size_t b = 0;
-    int st = plan_estimate_bytes(r->dim, r->nmodes, r->eps, r->prec, mcap, &b);
+    int st = plan_estimate_bytes(r->dim, r->nmodes, r->eps, r->prec, mcap, &b, r->upsampfac == 1.25 ? 1.25 : 2.0);
     if (st < 0) return st;
     *bytes = b + scratch_bytes(r, mcap);
     return NUFFT_OK;
@@ -198,7 +216,10 @@ struct GpuExecutor {
     if (!e) return NUFFT_ERR_ALLOC;
     e->kind = r->kind;
     int type = r->kind == NUFFT_REQ_TYPE1 ? 1 : 2;
-    int st = nufft_makeplan(type, r->dim, r->nmodes, r->isign, 1, r->eps, r->prec, ex->streams[0], nullptr, &e->p);
+    nufft_opts o;
+    nufft_default_opts(&o);
+    o.upsampfac = r->upsampfac == 1.25 ? 1.25 : 2.0;
+    int st = nufft_makeplan(type, r->dim, r->nmodes, r->isign, 1, r->eps, r->prec, ex->streams[0], &o, &e->p);
     if (st < 0) {
       e->p = nullptr;
       free_entry(e);
@@ -612,9 +633,13 @@ extern "C" {
 
 double nufft_server_clock(void) { return now_s(); }
 
+double nufft_request_upsampfac(const nufft_request* r) { return valid_shape(r) ? choose_sigma(r) : 0.0; }
+
 int nufft_request_bytes(const nufft_request* r, int64_t mcap, size_t* bytes) {
   if (!valid_shape(r) || !bytes || mcap < r->M) return NUFFT_ERR_BAD_ARG;
-  return GpuExecutor::estimate(nullptr, r, mcap, bytes);
+  nufft_request q = *r;
+  q.upsampfac = choose_sigma(r);
+  return GpuExecutor::estimate(nullptr, &q, mcap, bytes);
 }
 
 int nufft_server_create(size_t budget_bytes, int max_inflight, double timeout_s, nufft_server* out) {
@@ -680,6 +705,7 @@ int nufft_server_submit(nufft_server s, const nufft_request* r, int64_t* ticket)
   nufft_server_s::Req* q = new (std::nothrow) nufft_server_s::Req();
   if (!q) return NUFFT_ERR_ALLOC;
   q->r = *r;
+  q->r.upsampfac = choose_sigma(r);  // resolved once: the key, the estimate and the plan all use it
   q->t_submit = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {

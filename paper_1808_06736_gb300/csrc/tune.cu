@@ -1,13 +1,14 @@
 // Autotuner: time launch configurations on the caller's own data and keep
 // the fastest.  The tunables are the bin extents (which also fix the
 // shared-memory tile, bin + w per dimension), the largest subproblem, the
-// threads per block and the threshold below which a subproblem runs one per
+// threads per block, the threshold below which a subproblem runs one per
 // warp (the per-warp path's lanes cooperate on a point's stencil, the tiled
-// path gives each thread its own points).  The search is staged: bin shapes
-// first, then the subproblem size, the sparse threshold and the block size,
-// each stage starting from the best configuration so far.  The default
-// configuration is always timed first, so the result is never slower than it
-// as measured.
+// path gives each thread its own points) and the upsampling factor (2, or
+// 5/4 where eps allows: a grid about 4x smaller in 3D for a wider kernel).
+// The search is staged: bin shapes first, then the subproblem size, the
+// sparse threshold, the block size and the upsampling factor, each stage
+// starting from the best configuration so far.  The default configuration is
+// always timed first, so the result is never slower than it as measured.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,8 +90,8 @@ double time_trial(Trial& t, const nufft_opts& o, cudaStream_t st, int reps) {
   return ok ? best : -1.0;
 }
 
-int search(int dim, bool dbl, int w, Trial& t, cudaStream_t st, int reps, nufft_opts* best, double* best_ms,
-           double* default_ms) {
+int search(int dim, bool dbl, int w, bool try_sigma54, Trial& t, cudaStream_t st, int reps, nufft_opts* best,
+           double* best_ms, double* default_ms) {
   nufft_opts cur;
   nufft_default_opts(&cur);
   double cur_ms = time_trial(t, cur, st, reps);
@@ -123,6 +124,12 @@ int search(int dim, bool dbl, int w, Trial& t, cudaStream_t st, int reps, nufft_
   {
     nufft_opts o = cur;
     o.threads = 128;
+    consider(o);
+  }
+  if (try_sigma54) {  // smaller grids and FFTs for a wider kernel; its own default bins
+    nufft_opts o = cur;
+    o.upsampfac = 1.25;
+    o.bin_size[0] = o.bin_size[1] = o.bin_size[2] = 0;
     consider(o);
   }
   *best = cur;
@@ -199,6 +206,7 @@ int nufft_tune(int type, int dim, const int64_t* nmodes, int isign, double eps, 
   int64_t n[3] = {1, 1, 1};
   int st = nufft_choose_params(dim, nmodes, eps, prec, &w, &beta, n);
   if (st < 0) return st;
+  const bool s54 = nufft_choose_params_sigma(dim, nmodes, eps, prec, 1.25, nullptr, nullptr, nullptr) == NUFFT_OK;
   PlanTrial t;
   t.type = type;
   t.dim = dim;
@@ -213,7 +221,7 @@ int nufft_tune(int type, int dim, const int64_t* nmodes, int isign, double eps, 
   t.in = in;
   t.out = out;
   t.st = (cudaStream_t)stream;
-  return search(dim, prec == NUFFT_C128, w, t, t.st, reps, best, best_ms, default_ms);
+  return search(dim, prec == NUFFT_C128, w, s54, t, t.st, reps, best, best_ms, default_ms);
 }
 
 int nufft_batch_tune(int type, int dim, int B, const int64_t* nmodes, int isign, double eps, int prec,
@@ -227,6 +235,7 @@ int nufft_batch_tune(int type, int dim, int B, const int64_t* nmodes, int isign,
   int64_t n[3] = {1, 1, 1};
   int st = nufft_choose_params(dim, nmodes, eps, prec, &w, &beta, n);  // w depends on eps only
   if (st < 0) return st;
+  const bool s54 = nufft_choose_params_sigma(dim, nmodes, eps, prec, 1.25, nullptr, nullptr, nullptr) == NUFFT_OK;
   BatchTrial t;
   t.type = type;
   t.dim = dim;
@@ -242,7 +251,7 @@ int nufft_batch_tune(int type, int dim, int B, const int64_t* nmodes, int isign,
   t.in = in;
   t.out = out;
   t.st = (cudaStream_t)stream;
-  return search(dim, prec == NUFFT_C128, w, t, t.st, reps, best, best_ms, default_ms);
+  return search(dim, prec == NUFFT_C128, w, s54, t, t.st, reps, best, best_ms, default_ms);
 }
 
 }  // extern "C"

@@ -12,7 +12,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass, field
 
-from . import NufftError, NUFFT_C64, NUFFT_C128, _L as _base_lib
+from . import NufftError, NUFFT_C64, NUFFT_C128, _L as _base_lib  # noqa: F401 (re-exported)
 
 NUFFT_REQ_TYPE1 = 1
 NUFFT_REQ_TYPE2 = 2
@@ -25,7 +25,8 @@ NUFFT_ERR_SHUTDOWN = -10
 
 class nufft_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("flags", ctypes.c_int), ("dim", ctypes.c_int), ("nmodes", ctypes.c_int64 * 3),
-                ("isign", ctypes.c_int), ("prec", ctypes.c_int), ("eps", ctypes.c_double), ("M", ctypes.c_int64),
+                ("isign", ctypes.c_int), ("prec", ctypes.c_int), ("eps", ctypes.c_double),
+                ("upsampfac", ctypes.c_double), ("M", ctypes.c_int64),
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("in_", ctypes.c_void_p), ("in2", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("out2", ctypes.c_void_p), ("out3", ctypes.c_void_p), ("points_key", ctypes.c_uint64),
@@ -79,6 +80,8 @@ def _L():
         lib.nufft_server_complete.argtypes = [vp, i64, i32]
         lib.nufft_server_complete.restype = None
         lib.nufft_request_bytes.argtypes = [ctypes.POINTER(nufft_request), i64, ctypes.POINTER(ctypes.c_size_t)]
+        lib.nufft_request_upsampfac.argtypes = [ctypes.POINTER(nufft_request)]
+        lib.nufft_request_upsampfac.restype = dbl
         _ready = True
     return lib
 
@@ -138,10 +141,20 @@ def nufft_request_bytes(req: nufft_request, mcap: int):
     return st, b.value
 
 
+def nufft_request_upsampfac(req: nufft_request) -> float:
+    return float(_L().nufft_request_upsampfac(ctypes.byref(req)))
+
+
+def upsampfac_for(kind: int, n_modes, eps: float, M: int, prec: int = NUFFT_C64, upsampfac: float = 0.0) -> float:
+    """The upsampling factor the server would use for such a request."""
+    return nufft_request_upsampfac(make_request(kind, len(n_modes), n_modes, -1, prec, eps, M, upsampfac=upsampfac))
+
+
 def make_request(kind: int, dim: int, n_modes, isign: int, prec: int, eps: float, M: int, tag: int = 0,
-                 points_key: int = 0, flags: int = 0) -> nufft_request:
+                 points_key: int = 0, flags: int = 0, upsampfac: float = 0.0) -> nufft_request:
     r = nufft_request()
     r.flags = int(flags)
+    r.upsampfac = float(upsampfac)
     r.kind, r.dim, r.isign, r.prec, r.eps, r.M = int(kind), int(dim), int(isign), int(prec), float(eps), int(M)
     for i, v in enumerate(n_modes):
         r.nmodes[i] = int(v)
@@ -201,7 +214,8 @@ class Server:
             xs = list(x)
         return [torch.as_tensor(v).to(device=self.device, dtype=rdt).contiguous() for v in xs]
 
-    def _submit(self, kind, xs, data, n_modes, eps, isign, dtype, y=None, points_key=0, tag=0, flags=0):
+    def _submit(self, kind, xs, data, n_modes, eps, isign, dtype, y=None, points_key=0, tag=0, flags=0,
+                upsampfac=0.0):
         torch = self._torch
         cdt = dtype
         rdt = torch.float32 if cdt == torch.complex64 else torch.float64
@@ -211,7 +225,8 @@ class Server:
             d = len(xs)
             M = xs[0].numel()
             data = torch.as_tensor(data).to(device=self.device, dtype=cdt).contiguous()
-            r = make_request(kind, d, n_modes, isign, prec, eps, M, tag=tag, points_key=points_key, flags=flags)
+            r = make_request(kind, d, n_modes, isign, prec, eps, M, tag=tag, points_key=points_key, flags=flags,
+                             upsampfac=upsampfac)
             ptr = [v.data_ptr() for v in xs] + [0] * (3 - d)
             r.x, r.y, r.z = ptr
             r.in_ = data.data_ptr()
@@ -242,16 +257,19 @@ class Server:
         self._live[ticket] = (keep, outs, ev)
         return ticket
 
-    def type1(self, x, c, n_modes, eps=1e-6, isign=1, dtype=None, points_key=0, tag=0):
+    # upsampfac: 2 or 1.25, or 0 (the server picks per request, see nufft_request_upsampfac)
+    def type1(self, x, c, n_modes, eps=1e-6, isign=1, dtype=None, points_key=0, tag=0, upsampfac=0.0):
         dtype = dtype or self._torch.complex64
-        return self._submit(NUFFT_REQ_TYPE1, x, c, n_modes, eps, isign, dtype, points_key=points_key, tag=tag)
+        return self._submit(NUFFT_REQ_TYPE1, x, c, n_modes, eps, isign, dtype, points_key=points_key, tag=tag,
+                            upsampfac=upsampfac)
 
-    def type2(self, x, f, eps=1e-6, isign=-1, dtype=None, points_key=0, tag=0):
+    def type2(self, x, f, eps=1e-6, isign=-1, dtype=None, points_key=0, tag=0, upsampfac=0.0):
         dtype = dtype or self._torch.complex64
         n_modes = tuple(reversed(f.shape))
-        return self._submit(NUFFT_REQ_TYPE2, x, f, n_modes, eps, isign, dtype, points_key=points_key, tag=tag)
+        return self._submit(NUFFT_REQ_TYPE2, x, f, n_modes, eps, isign, dtype, points_key=points_key, tag=tag,
+                            upsampfac=upsampfac)
 
-    def lsq_grad(self, x, f, y, eps=1e-6, isign=-1, dtype=None, points_key=0, tag=0, xgrad="exact"):
+    def lsq_grad(self, x, f, y, eps=1e-6, isign=-1, dtype=None, points_key=0, tag=0, xgrad="exact", upsampfac=0.0):
         """loss = ||F2_isign(f; x) - y||^2 with its gradients in f and in the points
         (``xgrad``: "exact" or "kernel", as in the autograd functions)."""
         if xgrad not in ("exact", "kernel"):
@@ -259,7 +277,7 @@ class Server:
         dtype = dtype or self._torch.complex64
         n_modes = tuple(reversed(f.shape))
         return self._submit(NUFFT_REQ_LSQ_GRAD, x, f, n_modes, eps, isign, dtype, y=y, points_key=points_key,
-                            tag=tag, flags=NUFFT_FLAG_XGRAD_KERNEL if xgrad == "kernel" else 0)
+                            tag=tag, flags=NUFFT_FLAG_XGRAD_KERNEL if xgrad == "kernel" else 0, upsampfac=upsampfac)
 
     def poll(self, max_n: int = 256, wait_s: float = 0.0):
         st, cs = nufft_server_poll(self._h, max_n, wait_s)

@@ -108,3 +108,25 @@ def test_tune_candidates_host_only(lib):
     assert lib.nufft_tune_candidates(3, lib.NUFFT_C128, 16)[0] < lib.nufft_tune_candidates(3, lib.NUFFT_C64, 2)[0]
     assert lib.nufft_tune_candidates(4, lib.NUFFT_C64, 6)[0] == -1
     assert lib.nufft_tune_candidates(2, lib.NUFFT_C64, 17)[0] == -1
+
+
+def test_choose_params_sigma54_matches_oracle(lib, oracle_mod):
+    for eps in [0.1, 1e-2, 3e-3, 1e-3, 1e-4, 1e-5, 2e-6, 1e-6, 1e-7, 1e-8, 1e-9]:
+        for Ns in ([1], [7], [100], [256], [1000, 3], [64, 64, 64], [33, 17, 250]):
+            st, w, beta, ns = lib.nufft_choose_params_sigma(len(Ns), Ns, eps, lib.NUFFT_C128, 1.25)
+            ow, obeta, ons = oracle_mod.choose_params(eps, Ns, 1.25)
+            assert st >= 0 and w == ow and abs(beta - obeta) < 1e-12 * obeta and ns == ons, (eps, Ns)
+    # sigma = 2 through the same entry point is the paper's rule
+    assert lib.nufft_choose_params_sigma(3, [64] * 3, 1e-5, lib.NUFFT_C64, 2.0)[1:] == \
+        lib.nufft_choose_params(3, [64] * 3, 1e-5, lib.NUFFT_C64)[1:]
+    # rounding amplified by rmax^dim (Eq. (rmax)) beyond eps: warning (complex64 3D at 1e-4, not at 1e-3;
+    # complex128 3D at 1e-9, not at 1e-6)
+    assert lib.nufft_choose_params_sigma(3, [64] * 3, 1e-3, lib.NUFFT_C64, 1.25)[0] == 0
+    assert lib.nufft_choose_params_sigma(3, [64] * 3, 1e-4, lib.NUFFT_C64, 1.25)[0] == 1
+    assert lib.nufft_choose_params_sigma(1, [64], 1e-5, lib.NUFFT_C64, 1.25)[0] == 0
+    assert lib.nufft_choose_params_sigma(3, [64] * 3, 1e-6, lib.NUFFT_C128, 1.25)[0] == 0
+    assert lib.nufft_choose_params_sigma(3, [64] * 3, 1e-9, lib.NUFFT_C128, 1.25)[0] == 1
+    # w > 16 needed: warning, w clamped; any other sigma: bad argument
+    st, w, _, _ = lib.nufft_choose_params_sigma(1, [100], 1e-11, lib.NUFFT_C128, 1.25)
+    assert st == 1 and w == 16
+    assert lib.nufft_choose_params_sigma(1, [100], 1e-5, lib.NUFFT_C64, 1.5)[0] == -1

@@ -306,7 +306,7 @@ def test_planted_mistakes_are_caught(oracle_mod, monkeypatch):
     monkeypatch.setattr(oracle_mod, "dft", orig_dft)
     # (c) beta off by 10 percent (a mis-typed 2.30)
     orig_beta = oracle_mod.es_beta
-    monkeypatch.setattr(oracle_mod, "es_beta", lambda w: 2.07 * w)
+    monkeypatch.setattr(oracle_mod, "es_beta", lambda w, sigma=2.0: 2.07 * w)
     assert _err_t1(oracle_mod) > 2 * base  # and test_beta_golden fails too
     monkeypatch.setattr(oracle_mod, "es_beta", orig_beta)
     # (d) each dimension's correction computed with another dimension's fine-grid size
@@ -323,3 +323,59 @@ def test_planted_mistakes_are_caught(oracle_mod, monkeypatch):
     assert _err_t1(oracle_mod) > 1e-1
     monkeypatch.setattr(oracle_mod, "spread", orig_spread)
     assert _err_t1(oracle_mod) == pytest.approx(base)
+
+
+# ------------------------------------------------ upsampling factor sigma = 5/4
+def test_eserr_slope_golden(oracle_mod):
+    """The slope of Eq. (ESerr) that the sigma = 5/4 width rule uses, checked at sigma = 2
+    against the value the paper prints."""
+    (row,) = [r for r in _golden() if r[0] == "slope"]
+    sigma, slope = float(row[1]), float(row[2])
+    assert abs(oracle_mod.eserr_slope(sigma) - slope) < 1e-3
+    # and Eq. (gam) with the same gamma gives the paper's 2.30
+    assert abs(oracle_mod.GAMMA * math.pi * (1 - 1 / (2 * 2.0)) - 2.30) < 1e-3
+
+
+@pytest.mark.parametrize("w", [4, 6, 9, 11, 13, 16])
+def test_kernel_ft_at_sigma54_frequencies(oracle_mod, w):
+    """The GL rule stays accurate up to the largest correction frequency at sigma = 5/4,
+    alpha N/2 = pi w / (2 sigma) = 0.4 pi w, far below the tolerance that w serves."""
+    beta = oracle_mod.es_beta(w, 1.25)
+    xi = np.linspace(0.0, 0.4 * math.pi * w, 9)
+    gl = oracle_mod.kernel_ft(xi, w, beta)
+    ref = np.array([_es_ft_adaptive(beta, v) for v in xi])
+    err = np.max(np.abs(gl - ref) / np.abs(ref))
+    assert err < 1e-2 * 10.0 ** (-w / oracle_mod.eserr_slope(1.25)), err
+
+
+def _heuristic_eps_inf_sigma(oracle_mod, eps, Ns, sigma):
+    w, beta, ns = oracle_mod.choose_params(eps, Ns, sigma)
+    out = 0.0
+    for N, n in zip(Ns, ns):
+        a = math.pi * w / n
+        out = max(out, abs(_es_ft_adaptive(beta, a * (n - N / 2)) / _es_ft_adaptive(beta, a * N / 2)))
+    return out
+
+
+CASES54 = [(1, [200], 400), (2, [40, 33], 500), (3, [32, 28, 24], 600)]
+
+
+@pytest.mark.parametrize("d,Ns,M", CASES54)
+@pytest.mark.parametrize("eps", [1e-3, 1e-5, 1e-7, 1e-9])
+def test_o2_sigma54_error_vs_truth(oracle_mod, d, Ns, M, eps):
+    """sigma = 5/4 (reading R15: w from the slope of Eq. (ESerr) plus a calibrated offset, beta
+    from Eq. (gam)): the error against the exact sums is within 10 eps, not far below eps
+    (a grid or width mistake would overshoot), and within the heuristic level of Remark
+    r:heur evaluated at this sigma."""
+    xs = I.points(11, M, d)
+    c = I.complex_normal(12, M)
+    f = I.complex_normal(13, int(np.prod(Ns)))
+    w, beta, ns = oracle_mod.choose_params(eps, Ns, 1.25)
+    low = all(n < 2 * N for n, N in zip(ns, Ns))  # else 2w sets some n_i and the error drops further
+    heur = _heuristic_eps_inf_sigma(oracle_mod, eps, Ns, 1.25)
+    e1 = oracle_mod.rel_l2(oracle_mod.type1(xs, c, 1, Ns, w=w, beta=beta, ns=ns), oracle_mod.direct_type1(xs, c, 1, Ns))
+    e2 = oracle_mod.rel_l2(oracle_mod.type2(xs, f, -1, Ns, w=w, beta=beta, ns=ns), oracle_mod.direct_type2(xs, f, -1, Ns))
+    for e in (e1, e2):
+        assert e <= 10 * eps, (e, eps)
+        assert not low or e > eps / 100, (e, eps)
+        assert heur / 20 < e < 1.5 * heur, (e, heur)

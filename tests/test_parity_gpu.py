@@ -302,3 +302,36 @@ def test_execute_grad_rejects_type1_plan(pkg):
     p.setpts(torch.zeros(10, device="cuda:0"), torch.zeros(10, device="cuda:0"))
     assert pkg.nufft_execute_grad(p._h, 1, 1, 1) == -1
     p.close()
+
+
+# the cases where the library does not warn about rounding amplification at sigma = 5/4
+SIGMA54_CASES = [(1, np.complex64, 1e-5), (1, np.complex64, 1e-3), (2, np.complex64, 1e-3), (3, np.complex64, 1e-3),
+                 (1, np.complex128, 1e-9), (2, np.complex128, 1e-9), (3, np.complex128, 1e-6)]
+
+
+@pytest.mark.parametrize("d,cdtype,eps", SIGMA54_CASES)
+def test_parity_sigma54(pkg, oracle_mod, cdtype, eps, d):
+    """Upsampling factor 5/4 (opts.upsampfac): same (w, beta, n) as the oracle's rule, against
+    the exact sums (10 eps) and against O2 at identical parameters (rounding budget)."""
+    Ns, M = {1: ([1000], 6000), 2: ([70, 45], 20000), 3: ([24, 20, 16], 30000)}[d]
+    xs, c, f = case_inputs(d, Ns, M, "uniform", cdtype, seed=5000 + 10 * d)
+    x64 = [v.astype(np.float64) for v in xs]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns, 1.25)
+    prec = pkg.NUFFT_C64 if cdtype == np.complex64 else pkg.NUFFT_C128
+    assert pkg.nufft_choose_params_sigma(d, Ns, eps, prec, 1.25)[0] == 0
+    g1, info = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, upsampfac=1.25)
+    assert info["w"] == w and info["n"] == ns and abs(info["beta"] - beta) < 1e-9 * beta
+    g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, upsampfac=1.25)
+    bar = 10 * max(eps, 2e-6 if cdtype == np.complex64 else 0)
+    assert oracle_mod.rel_l2(g1[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= bar
+    assert oracle_mod.rel_l2(g2[0], oracle_mod.direct_type2(x64, f, -1, Ns)) <= bar
+    o2_1 = oracle_mod.type1(x64, c, 1, Ns, w=w, beta=beta, ns=ns)
+    o2_2 = oracle_mod.type2(x64, f, -1, Ns, w=w, beta=beta, ns=ns)
+    # the correction p_k amplifies the grid's rounding by up to rmax = phi^(0) / phi^(pi w / 2 sigma)
+    # (Eq. (rmax)): about e^{0.25 beta} at sigma = 5/4 against e^{0.057 beta} at 2, so the rounding
+    # budget grows by the ratio of the two
+    w2, b2, _ = oracle_mod.choose_params(eps, Ns)
+    rmax = lambda ww, bb, sg: float(oracle_mod.kernel_ft([0.0], ww, bb)[0] / oracle_mod.kernel_ft([math.pi * ww / (2 * sg)], ww, bb)[0])
+    tol = TOL_SAME[cdtype] * rmax(w, beta, 1.25) / rmax(w2, b2, 2.0)
+    assert oracle_mod.rel_l2(g1[0], o2_1) <= tol
+    assert oracle_mod.rel_l2(g2[0], o2_2) <= tol

@@ -121,7 +121,10 @@ def test_mix_equals_alone_and_is_right(pkg, oracle_mod):
     for i, q in enumerate(reqs):
         if q["kind"] == 3:
             continue
-        plan = p.Plan(q["kind"], q["modes"], eps=q["eps"], isign=q["isign"], dtype=q["dtype"], device="cuda:0")
+        prec = S.NUFFT_C128 if q["dtype"] == torch.complex128 else S.NUFFT_C64
+        sigma = S.upsampfac_for(q["kind"], q["modes"], q["eps"], q["M"], prec)  # the server's per-request choice
+        plan = p.Plan(q["kind"], q["modes"], eps=q["eps"], isign=q["isign"], dtype=q["dtype"], device="cuda:0",
+                      upsampfac=sigma)
         plan.setpts(*q["x"])
         ref = plan.execute(q["data"]).reshape(-1)
         plan.close()
@@ -171,8 +174,9 @@ def test_lsq_gradient_request_3d_against_direct_sums(pkg, oracle_mod, cdt, eps, 
     # the kernel route's point gradient: ~2 sqrt(12) times the values' error (aliased
     # frequencies weighted by their own size), bar 20 eps with an fp32 floor
     tol_x = tol if xgrad == "exact" else 20 * max(eps, 1e-5 if cdt == "c64" else 0)
-    # loss against the plan path's forward values
-    plan = p.Plan(2, Ns, eps=eps, isign=-1, dtype=cdtype, device=dev)
+    # loss against the plan path's forward values, on the fine grid the server chose
+    sigma = S.upsampfac_for(S.NUFFT_REQ_LSQ_GRAD, Ns, eps, M, S.NUFFT_C128 if cdt == "c128" else S.NUFFT_C64)
+    plan = p.Plan(2, Ns, eps=eps, isign=-1, dtype=cdtype, device=dev, upsampfac=sigma)
     plan.setpts(*xs)
     cv = plan.execute(f).reshape(-1)
     plan.close()

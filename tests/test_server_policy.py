@@ -105,8 +105,8 @@ class Fake:
             self.busy.discard(eid)
         S.nufft_server_complete(self.h, ticket, status)
 
-    def submit(self, M=1000, n=(8, 8), kind=1, points_key=0, tag=0):
-        r = S.make_request(kind, len(n), n, 1, 1, 1e-5, M, tag=tag, points_key=points_key)
+    def submit(self, M=1000, n=(8, 8), kind=1, points_key=0, tag=0, eps=1e-5):
+        r = S.make_request(kind, len(n), n, 1, 1, eps, M, tag=tag, points_key=points_key)
         r.x = r.y = r.z = 1
         r.in_ = r.out = 1
         st, t = S.nufft_server_submit(self.h, r)
@@ -304,7 +304,7 @@ def test_randomised_stress_invariants():
 
 def test_request_bytes_estimate_counts_grid_and_points():
     # host-only: 3D N = 64^3 complex64 at eps 1e-5 -> fine grid 128^3 (w = 6)
-    r = S.make_request(2, 3, (64, 64, 64), -1, 1, 1e-5, 100000)
+    r = S.make_request(2, 3, (64, 64, 64), -1, 1, 1e-5, 100000, upsampfac=2.0)
     st, b = S.nufft_request_bytes(r, 131072)
     assert st == 0
     grid = 128 ** 3 * 8
@@ -312,7 +312,40 @@ def test_request_bytes_estimate_counts_grid_and_points():
     assert b <= 2 * grid + 131072 * 16 + 8 * 2 ** 20
     st, b2 = S.nufft_request_bytes(r, 262144)
     assert b2 - b >= 131072 * 16
-    r3 = S.make_request(3, 3, (64, 64, 64), -1, 1, 1e-5, 100000)
+    r3 = S.make_request(3, 3, (64, 64, 64), -1, 1, 1e-5, 100000, upsampfac=2.0)
     st, b3 = S.nufft_request_bytes(r3, 131072)
     assert b3 - b == ((2 + 3) * 131072 + 64 ** 3) * 8  # gradient scratch
     assert S.nufft_request_bytes(r, 10)[0] == -1  # capacity below M
+
+
+def test_upsampling_choice_per_request():
+    """upsampfac 0: 5/4 when the fine-grid work saved outweighs the wider kernel's extra
+    stencil cells (few points on a big grid), 2 otherwise, and never 5/4 when eps would need
+    w > 16 there; explicit values pass through; requests with different factors do not share
+    plan entries, and the estimate follows the smaller grid."""
+    pick = lambda M, eps=1e-3, n=(256, 256, 256), sig=0.0, prec=1: S.upsampfac_for(1, n, eps, M, prec, upsampfac=sig)
+    assert pick(10 ** 5) == 1.25 and pick(10 ** 6) == 1.25
+    assert pick(10 ** 8) == 2.0
+    # complex64 3D at 1e-5: the correction would amplify rounding past eps (Eq. (rmax)); complex128 is fine
+    assert pick(10 ** 5, eps=1e-5) == 2.0 and pick(10 ** 5, eps=1e-5, prec=2) == 1.25
+    assert pick(10 ** 5, eps=1e-11, prec=2) == 2.0
+    assert pick(10 ** 8, sig=1.25) == 1.25 and pick(10 ** 5, sig=2.0) == 2.0
+    r = S.make_request(1, 3, (256, 256, 256), 1, 1, 1e-5, 10 ** 5, upsampfac=1.5)
+    assert S.nufft_request_upsampfac(r) == 0.0
+    st2, b2 = S.nufft_request_bytes(S.make_request(1, 3, (256,) * 3, 1, 1, 1e-3, 10 ** 5, upsampfac=2.0), 2 ** 17)
+    st5, b5 = S.nufft_request_bytes(S.make_request(1, 3, (256,) * 3, 1, 1, 1e-3, 10 ** 5), 2 ** 17)
+    assert st2 == 0 and st5 == 0 and b5 < b2 / 3
+    f = Fake(budget=10 ** 12, max_inflight=1)
+    t1 = f.submit(M=1000, n=(512, 512), eps=1e-3)  # same shape, two factors: two entries
+    assert f.wait_launches(1)
+    f.complete(t1)
+    r = S.make_request(1, 2, (512, 512), 1, 1, 1e-3, 1000, upsampfac=2.0)
+    r.x = r.y = r.z = r.in_ = r.out = 1
+    st, t2 = S.nufft_server_submit(f.h, r)
+    assert st == 0 and f.wait_launches(2)
+    f.complete(t2)
+    f.poll_all(2)
+    keys = [c[1] for c in f.created]
+    f.close()
+    assert len(f.created) == 2 and keys[0][:5] == keys[1][:5], keys
+    assert not f.errors
