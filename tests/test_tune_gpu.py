@@ -30,7 +30,8 @@ def test_tuned_plan_is_correct_and_not_slower(pkg, oracle_mod, typ, d, Ns, M):
     data = I.torch_complex_normal(910 + d, M if typ == 1 else ntot, dev, torch.complex64)
     opts, best, default = pkg.tune_plan(typ, Ns, xs, data, eps=1e-5, reps=2)
     assert 0 < best <= default
-    ref = pkg.Plan(typ, Ns, eps=1e-5, device=dev)
+    # the reference plan uses the grid the tuner picked (upsampling 2 or 5/4); only launch shapes differ
+    ref = pkg.Plan(typ, Ns, eps=1e-5, device=dev, upsampfac=opts["upsampfac"])
     ref.setpts(*xs)
     r = ref.execute(data).reshape(-1)
     ref.close()
@@ -74,7 +75,7 @@ def test_tuned_batch_is_correct_and_not_slower(pkg):
     moffs = bp.mode_offsets
     bp.close()
     for t in range(B):
-        p = pkg.Plan(2, modes[t], eps=1e-5, device=dev)
+        p = pkg.Plan(2, modes[t], eps=1e-5, device=dev, upsampfac=opts["upsampfac"])
         p.setpts(*[v[int(offs[t]):int(offs[t + 1])] for v in xs])
         r = p.execute(f[moffs[t]:moffs[t + 1]]).reshape(-1)
         p.close()
