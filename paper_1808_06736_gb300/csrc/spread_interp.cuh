@@ -26,6 +26,7 @@
 // the tile result does not depend on the order of the atomics.
 #pragma once
 
+#include "df.cuh"
 #include "nufft_internal.cuh"
 
 namespace nufft {
@@ -569,6 +570,166 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T k
   }
 }
 
+// ------------------------------------------------ interp, complex128
+// The GB300 runs FP64 at about 1/60 of its FP32 rate, so the complex128
+// interpolation runs in double-float arithmetic on the FP32 pipe (df.cuh):
+// the kernel values (square root, exponential) and the w^d-term tensor
+// contraction; every tile value and weight is a pair (hi, lo) of floats with
+// hi + lo equal to the double to ~2^-48.  That is accurate to ~1e-14
+// relative, far below the eps >= 1e-11 the complex128 path serves.  The tile
+// is scaled by a power of two so its largest value is about 1 (float range;
+// the scale is undone exactly on output).
+// kernel values along one dimension in double-float (see point_weights)
+template <int W>
+__device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int& ts, DF* k) {
+  const int il = min((int)v, B - 1);
+  const double f = v - double(il);
+  const int s = stencil_step<W>(f);
+  ts = il + s;
+  const DF fd = df_of(f);
+  const DF scale = DF{2.0f / W, __double2float_rn(2.0 / W - (double)(2.0f / W))};
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    // z = (t - floor(w/2) + step - f) 2 / w in double-float
+    const DF z = df_mul(df_add(DF{(float)(t - W / 2 + s), 0.0f}, DF{-fd.hi, -fd.lo}), scale);
+    k[t] = es_eval_df_z(z, beta);
+  }
+}
+
+template <int D, int W>
+__global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, double kpar, Sorted s, const double2* __restrict__ grid,
+                                                      double2* __restrict__ c, int* __restrict__ work, BatchTable bt) {
+  using Rec = typename Traits<double>::Rec;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int hist[NRES_INTERP];
+  __shared__ int s_sub, s_bin, s_maxexp;
+  __shared__ long long s_goff;
+  __shared__ Geom s_geo;
+
+  const int ntile = g.ntile, maxsub = g.maxsub;
+  double2* tile = reinterpret_cast<double2*>(smem);  // then, in place, float4 (re hi, re lo, im hi, im lo)
+  float4* tdf = reinterpret_cast<float4*>(smem);
+  Stage<double, D> st = carve_stage<double, D>(reinterpret_cast<unsigned char*>(tile + ntile), maxsub);
+  const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(s.rec);
+  const int T0 = g.T[0], T01 = g.T[0] * g.T[1];
+  const DF bdf = df_of(kpar);  // beta
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      next_subproblem(g, s, bt, work, &s_sub, &s_bin, &s_goff, &s_geo);
+      s_maxexp = -1100;
+    }
+    if (threadIdx.x < NRES_INTERP) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int sub = s_sub;
+    if (sub >= *s.nsub) break;
+    const int bin = s_bin, p0 = s.sub_pt0[sub], cnt = s.sub_cnt[sub];
+
+    int org[3];
+    tile_origin(s_geo, bin, org);
+    const int nrows = ntile / T0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int n0 = s_geo.n[0], n1 = s_geo.n[1], n2 = s_geo.n[2];
+    const double2* gridt = grid + s_goff;
+    for (int row = threadIdx.x >> 5; row < nrows; row += nw) {
+      const int t1 = row % g.T[1], t2 = row / g.T[1];
+      const long long gy = wrap_idx(org[1] + t1, n1);
+      const long long gz = wrap_idx(org[2] + t2, n2);
+      const double2* grow = gridt + (gz * n1 + gy) * (long long)n0;
+      for (int t0 = lane; t0 < T0; t0 += 32) cp_async_elem(tile + row * T0 + t0, grow + wrap_idx(org[0] + t0, n0));
+    }
+    cp_async_commit();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) stage_point<double, D, W, NRES_INTERP>(g, rec[p0 + q], q, st, hist);
+    cp_async_wait_all();
+    __syncthreads();
+    // power-of-two scale: the largest |value| of the tile to [0.5, 1)
+    int me = -1100;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const double2 v = tile[t];
+      const double m = fmax(fabs(v.x), fabs(v.y));
+      if (m > 0.0) me = max(me, ilogb(m) + 1);
+    }
+    atomicMax(&s_maxexp, me);
+    __syncthreads();
+    const int sh = s_maxexp > -1000 ? s_maxexp : 0;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const double2 v = tile[t];
+      const DF re = df_of(ldexp(v.x, -sh)), im = df_of(ldexp(v.y, -sh));
+      tdf[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    bucket_order<double, D, NRES_INTERP>(cnt, st, hist);  // synchronises
+
+    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+      const int q = st.order[sl];
+      const Rec rq = rec[p0 + q];
+      DF k0[W];
+      int ts0, ts1 = 0, ts2 = 0;
+      point_weights_df<W>(rq.v[0], g.B[0], bdf, ts0, k0);
+      DF k1[(D > 1) ? W : 1];
+      double f2 = 0.0;
+      int st2 = 0;
+      if constexpr (D > 1) {
+        point_weights_df<W>(rq.v[1], g.B[1], bdf, ts1, k1);
+      } else {
+        k1[0] = DF{1.0f, 0.0f};
+      }
+      if constexpr (D > 2) {
+        const double v2 = rq.v[2];
+        const int il2 = min((int)v2, g.B[2] - 1);
+        f2 = v2 - double(il2);
+        st2 = stencil_step<W>(f2);
+        ts2 = il2 + st2;
+      }
+      const int base = ts0 + T0 * ts1 + T01 * ts2;
+      constexpr int W1 = (D > 1) ? W : 1;
+      constexpr int W2 = (D > 2) ? W : 1;
+      DF ar = {0.f, 0.f}, ai = {0.f, 0.f};
+#pragma unroll 1
+      for (int l2 = 0; l2 < W2; ++l2) {
+        DF br = {0.f, 0.f}, bi = {0.f, 0.f};
+#pragma unroll
+        for (int l1 = 0; l1 < W1; ++l1) {
+          const float4* rowp = tdf + base + l1 * T0 + l2 * T01;
+          // even and odd nodes in separate accumulators: four independent
+          // dependency chains per point instead of two
+          DF sr0 = {0.f, 0.f}, si0 = {0.f, 0.f}, sr1 = {0.f, 0.f}, si1 = {0.f, 0.f};
+#pragma unroll
+          for (int l0 = 0; l0 < W; l0 += 2) {
+            const float4 gv = rowp[l0];
+            df_mac(sr0, DF{gv.x, gv.y}, k0[l0]);
+            df_mac(si0, DF{gv.z, gv.w}, k0[l0]);
+            if (l0 + 1 < W) {
+              const float4 gu = rowp[l0 + 1];
+              df_mac(sr1, DF{gu.x, gu.y}, k0[l0 + 1]);
+              df_mac(si1, DF{gu.z, gu.w}, k0[l0 + 1]);
+            }
+          }
+          const DF sr = df_add(df_norm(sr0), df_norm(sr1)), si = df_add(df_norm(si0), df_norm(si1));
+          df_mac(br, sr, k1[l1]);
+          df_mac(bi, si, k1[l1]);
+        }
+        DF k2 = {1.0f, 0.0f};
+        if constexpr (D > 2) k2 = es_eval_df(node_z<W>(l2, st2, f2), bdf);
+        df_mac(ar, df_norm(br), k2);
+        df_mac(ai, df_norm(bi), k2);
+      }
+      const double2 out = make_double2(ldexp((double)ar.hi + (double)ar.lo, sh), ldexp((double)ai.hi + (double)ai.lo, sh));
+      store_once(c + rq.idx, out);
+    }
+    __syncthreads();
+  }
+}
+
+// the tiled interpolation kernel for each precision
+template <typename T, int D, int W>
+struct InterpKernel {
+  static constexpr auto value = k_interp<T, D, W>;
+};
+template <int D, int W>
+struct InterpKernel<double, D, W> {
+  static constexpr auto value = k_interp_df<D, W>;
+};
+
 // ------------------------------------------------- sparse subproblems
 // Subproblems of at most 32 points (low point density: most bins hold a few
 // points or none) skip the shared-memory tile, whose zeroing, flushing or
@@ -844,7 +1005,7 @@ template <typename T, int D, int W>
 cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* grid, void* c,
                        int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
                        const BatchTable& bt) {
-  auto kern = k_interp<T, D, W>;
+  auto kern = InterpKernel<T, D, W>::value;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
