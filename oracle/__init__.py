@@ -68,6 +68,7 @@ def _L():
         i64 = ctypes.c_int64
         lib.oracle_type1_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ctypes.c_int, i64, ip, dp]
         lib.oracle_type2_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, ip, dp, ctypes.c_int, dp]
+        lib.oracle_type3_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ctypes.c_int, i64, dp, dp, dp, dp]
         lib.oracle_spread.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double, dp]
         lib.oracle_interp.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -159,6 +160,19 @@ def direct_type2(xs, f, isign: int, Ns) -> np.ndarray:
     _L().oracle_type2_direct(d, nt, _dptr(full[0]), _dptr(full[1]), _dptr(full[2]), _iptr(N),
                              _dptr(f.view(np.float64)), int(isign), _dptr(c.view(np.float64)))
     return c
+
+
+def direct_type3(xs, c, isign: int, ss) -> np.ndarray:
+    """Eq. (3): f_k = sum_j c_j exp(i isign s_k . x_j) for real frequencies ss (one array per dimension)."""
+    d, xs, full = _coords(xs)
+    _, ss, sfull = _coords(ss)
+    c = _cplx(c)
+    nt = ss[0].shape[0]
+    f = np.zeros(nt, dtype=np.complex128)
+    _L().oracle_type3_direct(d, c.shape[0], _dptr(full[0]), _dptr(full[1]), _dptr(full[2]),
+                             _dptr(c.view(np.float64)), int(isign), nt, _dptr(sfull[0]), _dptr(sfull[1]),
+                             _dptr(sfull[2]), _dptr(f.view(np.float64)))
+    return f
 
 
 # ---------------------------------------------------------- parameters (a0)
@@ -335,3 +349,58 @@ def type2(xs, f, isign: int, Ns, eps: float | None = None, w: int | None = None,
         w, beta, ns = choose_params(eps, Ns)
     b = dft(precorrect(f, Ns, ns, w, beta), isign)
     return interp(xs, b, ns, w, beta)
+
+
+# ------------------------------------------------------------- O2 type 3
+def type3_params(eps: float, xs, ss, sigma: float = 2.0):
+    """Sec. 3.3, step 0: centres x0, s0 (midpoints of the bounding boxes; the translation of
+    Eq. (trans) is always applied), half-widths X_i, S_i (Eq. (XS) after centring), fine grid
+    n_i = next235(max(2 sigma X_i S_i / pi + w, 2 w)) and dilation gamma_i = n_i / (2 sigma S_i)
+    (Eq. (ng)); a dimension with S_i = 0 takes the smallest gamma_i that keeps
+    X_i / gamma_i <= pi (1 - w / n_i) (Eq. (cond1)), or 1."""
+    w = kernel_width(eps, sigma)
+    beta = es_beta(w, sigma)
+    x0, s0, X, S, ns, gam = [], [], [], [], [], []
+    for xv, sv in zip(xs, ss):
+        xv = np.asarray(xv, dtype=np.float64)
+        sv = np.asarray(sv, dtype=np.float64)
+        xa, xb = float(xv.min()), float(xv.max())
+        sa, sb = float(sv.min()), float(sv.max())
+        x0.append(0.5 * (xa + xb))
+        s0.append(0.5 * (sa + sb))
+        Xi, Si = 0.5 * (xb - xa), 0.5 * (sb - sa)
+        n = next235(max(int(math.ceil(2.0 * sigma / math.pi * Xi * Si + w)), 2 * w))
+        if Si > 0:
+            g = n / (2.0 * sigma * Si)
+        else:
+            g = Xi / (math.pi * (1.0 - w / n)) if Xi > 0 else 1.0
+        X.append(Xi)
+        S.append(Si)
+        ns.append(n)
+        gam.append(g)
+    return dict(w=w, beta=beta, x0=x0, s0=s0, X=X, S=S, ns=ns, gamma=gam)
+
+
+def type3(xs, c, isign: int, ss, eps: float) -> np.ndarray:
+    """O2 type 3 (Sec. 3.3): translate (Eq. (trans)), dilate and spread onto the n_i grid
+    (step 1, Eq. (blt3)), evaluate that grid as a Fourier series at the rescaled targets
+    with the O2 type 2 (step 2, Eq. (bkt3)), correct by p_k = prod_i 2 / (w phi^(alpha_i s'_k))
+    (step 3), undo the translation."""
+    P = type3_params(eps, xs, ss)
+    w, beta, ns = P["w"], P["beta"], P["ns"]
+    d = len(xs)
+    xt = [np.asarray(xs[i], dtype=np.float64) - P["x0"][i] for i in range(d)]
+    st = [np.asarray(ss[i], dtype=np.float64) - P["s0"][i] for i in range(d)]
+    pre = np.exp(1j * isign * sum(P["s0"][i] * xt[i] for i in range(d)))
+    xp = [xt[i] / P["gamma"][i] for i in range(d)]
+    b = spread(xp, _cplx(c) * pre, ns, w, beta)          # grid index l <-> Fourier index l mod n
+    for ax, n in enumerate(reversed(ns)):                  # to increasing Fourier index
+        b = np.roll(b, n // 2, axis=ax)
+    spp = [2 * math.pi / ns[i] * P["gamma"][i] * st[i] for i in range(d)]
+    bk = type2(spp, b.ravel(), isign, ns, eps=eps)
+    p = np.ones(st[0].shape[0])
+    for i in range(d):
+        alpha = math.pi * w / ns[i]
+        p = p * 2.0 / (w * kernel_ft(alpha * P["gamma"][i] * st[i], w, beta))
+    post = np.exp(1j * isign * sum(np.asarray(ss[i], dtype=np.float64) * P["x0"][i] for i in range(d)))
+    return p * bk * post

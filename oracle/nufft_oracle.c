@@ -257,6 +257,29 @@ void oracle_interp(int d, int64_t M, const double* x, const double* y, const dou
   }
 }
 
+/*
+ * Eq. (3), the type-3 sum: f_k = sum_j c_j exp(i isign s_k . x_j) for nt
+ * real target frequencies (s, t, u = their coordinates), Kahan sums over the
+ * sources, threads over the targets.
+ */
+void oracle_type3_direct(int d, int64_t M, const double* x, const double* y, const double* z, const double* c,
+                         int isign, int64_t nt, const double* s, const double* t, const double* u, double* f) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t q = 0; q < nt; ++q) {
+    ksum re = {0, 0}, im = {0, 0};
+    for (int64_t j = 0; j < M; ++j) {
+      double ph = 0;
+      for (int i = 0; i < d; ++i) ph += coord(i, s, t, u)[q] * coord(i, x, y, z)[j];
+      ph *= (double)isign;
+      double cs = cos(ph), sn = sin(ph);
+      kadd(&re, c[2 * j] * cs - c[2 * j + 1] * sn);
+      kadd(&im, c[2 * j] * sn + c[2 * j + 1] * cs);
+    }
+    f[2 * q] = re.s;
+    f[2 * q + 1] = im.s;
+  }
+}
+
 /* Number of OpenMP threads the direct sums use (1 without OpenMP). */
 int oracle_num_threads(void) {
 #ifdef _OPENMP

@@ -379,3 +379,65 @@ def test_o2_sigma54_error_vs_truth(oracle_mod, d, Ns, M, eps):
         assert e <= 10 * eps, (e, eps)
         assert not low or e > eps / 100, (e, eps)
         assert heur / 20 < e < 1.5 * heur, (e, heur)
+
+
+# ------------------------------------------------------------------ type 3
+def test_direct_type3_integer_frequencies_equal_type1(oracle_mod):
+    """Eq. (3) at integer frequencies is Eq. (1) at those modes (two independent code paths)."""
+    rng = np.random.default_rng(31)
+    xs = [rng.uniform(-math.pi, math.pi, 300) for _ in range(2)]
+    c = I.complex_normal(32, 300)
+    modes = rng.integers(-20, 20, size=(50, 2))
+    for isign in (1, -1):
+        f1 = oracle_mod.direct_type1(xs, c, isign, [40, 40], modes=modes)
+        f3 = oracle_mod.direct_type3(xs, c, isign, [modes[:, 0].astype(float), modes[:, 1].astype(float)])
+        np.testing.assert_allclose(f3, f1, rtol=0, atol=1e-11 * np.abs(f1).max())
+
+
+def test_direct_type3_brute_force_and_translation(oracle_mod):
+    """Tiny inputs against a dense exponential matrix, and the translation identity Eq. (trans)."""
+    rng = np.random.default_rng(33)
+    x = [rng.uniform(-3, 7, 9), rng.uniform(0, 2, 9), rng.uniform(-1, 1, 9)]
+    s = [rng.uniform(-30, 5, 7), rng.uniform(-1, 1, 7), rng.uniform(10, 12, 7)]
+    c = I.complex_normal(34, 9)
+    ph = sum(np.outer(s[i], x[i]) for i in range(3))
+    for isign in (1, -1):
+        np.testing.assert_allclose(oracle_mod.direct_type3(x, c, isign, s), np.exp(1j * isign * ph) @ c,
+                                   rtol=1e-12, atol=1e-12)
+    x0, s0 = [0.3, -1.2, 2.0], [4.0, 0.5, -7.0]
+    lhs = oracle_mod.direct_type3([x[i] + x0[i] for i in range(3)], c, 1, [s[i] + s0[i] for i in range(3)])
+    pre = np.exp(1j * sum(s0[i] * x[i] for i in range(3)))
+    post = np.exp(1j * sum((s[i] + s0[i]) * x0[i] for i in range(3)))
+    np.testing.assert_allclose(lhs, post * oracle_mod.direct_type3(x, c * pre, 1, s), rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_type3_params_satisfy_the_paper_conditions(oracle_mod, eps):
+    """Eq. (cond1): rescaled sources stay w/2 cells from +-pi; Eq. (cond2): gamma S <= n / (2 sigma)."""
+    rng = np.random.default_rng(35)
+    xs = [rng.uniform(-50, 10, 100), rng.uniform(3, 4, 100)]
+    ss = [rng.uniform(-2, 9, 80), np.full(80, 5.0)]   # second dimension: all targets equal
+    P = oracle_mod.type3_params(eps, xs, ss)
+    for i in range(2):
+        n, g, X, S, w = P["ns"][i], P["gamma"][i], P["X"][i], P["S"][i], P["w"]
+        assert X / g <= math.pi * (1 - w / n) * (1 + 1e-12)
+        assert g * S <= n / 4.0 * (1 + 1e-12)
+        assert n >= 2 * w
+
+
+T3_CASES = [(1, 600, 500), (2, 700, 600), (3, 800, 700)]
+
+
+@pytest.mark.parametrize("d,M,N", T3_CASES)
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_o2_type3_error_vs_truth(oracle_mod, d, M, N, eps):
+    """Sec. 3.3's algorithm (O2) against the exact sum (O1): within 10 eps (the Remark after step 3:
+    using eps in steps 1 and 2 gives an overall error close to eps) and not far below eps.
+    Sources and targets are off-centre, so the translation of Eq. (trans) matters."""
+    rng = np.random.default_rng(40 + d)
+    xs = [rng.uniform(-2, 11, M) for _ in range(d)]
+    ss = [rng.uniform(-25, 8, N) for _ in range(d)]
+    c = I.complex_normal(41 + d, M)
+    for isign in (1, -1):
+        e = oracle_mod.rel_l2(oracle_mod.type3(xs, c, isign, ss, eps), oracle_mod.direct_type3(xs, c, isign, ss))
+        assert eps / 100 < e <= 10 * eps, (isign, e)
