@@ -272,6 +272,52 @@ int nufft_batch_tune(int type, int dim, int B, const int64_t* nmodes, int isign,
  * how many there are, or NUFFT_ERR_BAD_ARG. */
 int nufft_tune_candidates(int dim, int prec, int w, int* bins, int max);
 
+/* ------------------------------------------------------------------ type 3
+ * Type 3 (non-uniform to non-uniform, Sec. 1, Eq. (3)):
+ *   f_k = sum_{j=1..M} c_j exp(i isign s_k.x_j),  k = 1..N,
+ * with M source points x_j and N target frequencies s_k in R^d, both
+ * arbitrary finite reals (no periodicity, no range limit), computed by the
+ * algorithm of Sec. 3.3: translate both sets to their centres (Eq. (trans)),
+ * dilate the sources by gamma_i and spread them onto a fine grid of
+ * n_i = next235(max(2 sigma X_i S_i / pi + w, 2 w)) cells (Eq. (ng); X_i, S_i
+ * the half-widths of the two bounding boxes), evaluate that grid as a
+ * Fourier series at the rescaled targets with an inner type-2 plan (Eq.
+ * (bkt3)), and divide by the kernel's Fourier transform at the targets.
+ * The error is governed by eps as for types 1 and 2; the work grows with the
+ * space-bandwidth product X_i S_i, which fixes n_i.
+ *
+ * Same conventions as above: device pointers on the plan's device, caller
+ * keeps ownership, work enqueued on the plan's stream.  nufft3_setpts reads
+ * both bounding boxes back to the host (it synchronises the stream) and
+ * (re)allocates the grid, which may grow between calls.
+ */
+typedef struct nufft_plan3_s* nufft_plan3;
+
+/* dim 1..3; isign +1 / -1; eps and prec as for nufft_makeplan; opts may be
+ * NULL (defaults; bin_size, max_subprob, sparse_max, threads and upsampfac
+ * apply to the spreading step and to the inner type-2 plan).  Returns NUFFT_OK,
+ * NUFFT_WARN_EPS_TOO_SMALL, or an error (*out = NULL). */
+int nufft3_makeplan(int dim, int isign, double eps, int prec, void* stream, const nufft_opts* opts,
+                    nufft_plan3* out);
+/* Sources x, y, z (M reals each; y NULL if dim < 2, z NULL if dim < 3) and
+ * targets s, t, u (N reals each, likewise).  M = 0 or N = 0 is allowed.
+ * Returns NUFFT_OK; NUFFT_ERR_BAD_ARG (M < 0, N < 0, NULL pointer);
+ * NUFFT_ERR_OUT_OF_RANGE (a coordinate not finite); NUFFT_ERR_TOO_BIG (M or
+ * N >= 2^31, or a space-bandwidth product whose grid is too large);
+ * NUFFT_ERR_ALLOC / _CUDA / _CUFFT. */
+int nufft3_setpts(nufft_plan3 plan, int64_t M, const void* x, const void* y, const void* z, int64_t N,
+                  const void* s, const void* t, const void* u);
+/* c: M input strengths, f: N outputs (complex, device).  NUFFT_ERR_NOT_SET
+ * before nufft3_setpts. */
+int nufft3_execute(nufft_plan3 plan, const void* c, void* f);
+/* Kernel width, ES beta, and per dimension the fine grid n_i and dilation
+ * gamma_i chosen by the last nufft3_setpts (any pointer may be NULL). */
+int nufft3_plan_info(nufft_plan3 plan, int* w, double* beta, int64_t* n, double* gamma);
+/* Synchronise the plan's stream; return any error recorded on the device. */
+int nufft3_get_status(nufft_plan3 plan);
+/* Free the plan (NULL is allowed).  Synchronises its stream first. */
+int nufft3_destroy(nufft_plan3 plan);
+
 /* ------------------------------------------------------------ no allocation
  * nufft_spread_noalloc -- the spreading step of a complex64 type-1 transform
  * (fine-grid values b_l of Eq. (bl)) for callers that cannot allocate device

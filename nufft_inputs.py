@@ -8,7 +8,9 @@ Recipe (the paper uses no dataset; Sec. 6 draws its own synthetic points):
   * "uniform" points: x_i iid U[-pi, pi) per coordinate;
   * "clustered" points: x_i iid N(0, sigma^2) per coordinate (sigma = 0.3),
     wrapped into [-pi, pi);
-  * strengths / coefficients: real and imaginary parts iid N(0, 1).
+  * strengths / coefficients: real and imaginary parts iid N(0, 1);
+  * type-3 sources and frequencies: uniform (or clipped Gaussian) in an
+    off-centre box centre +- half per coordinate (box_points).
 Seeds are plain integers; every generator is numpy PCG64 (host) or torch's
 Philox generator (device, for the 1e7..1e8-point workloads).
 """
@@ -46,6 +48,23 @@ def points(seed: int, M: int, d: int, kind: str = "uniform", dtype=np.float64, s
         # float32 rounding can land on +pi; keep the half-open range
         v[v >= np.asarray(math.pi, dtype=dtype)] = np.asarray(-math.pi, dtype=dtype)
         out.append(v)
+    return out
+
+
+def box_points(seed: int, n: int, centre, half, kind: str = "uniform", dtype=np.float64):
+    """Type-3 sources or targets: len(centre) coordinate arrays of n reals in the box
+    centre_i +- half_i, iid uniform ('uniform') or Gaussian about the centre with
+    standard deviation half_i / 4 clipped to the box ('clustered')."""
+    g = rng(seed)
+    out = []
+    for c, h in zip(centre, half):
+        if kind == "uniform":
+            v = g.uniform(c - h, c + h, size=n)
+        elif kind == "clustered":
+            v = np.clip(g.normal(c, h / 4.0, size=n), c - h, c + h)
+        else:
+            raise ValueError(kind)
+        out.append(v.astype(dtype))
     return out
 
 

@@ -21,7 +21,8 @@ __all__ = [
     "nufft_strerror", "nufft_choose_params", "nufft_choose_params_sigma", "nufft_correction_factors", "nufft_next235",
     "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
     "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy", "nufft_tune", "nufft_batch_tune",
-    "nufft_tune_candidates", "opts_dict", "tune_plan", "tune_batch",
+    "nufft_tune_candidates", "opts_dict", "tune_plan", "tune_batch", "Plan3", "nufft3_makeplan", "nufft3_setpts",
+    "nufft3_execute", "nufft3_plan_info", "nufft3_get_status", "nufft3_destroy",
     "NUFFT_C64", "NUFFT_C128",
 ]
 
@@ -95,6 +96,12 @@ def _L():
     lib.nufft_batch_tune.argtypes = [i32, i32, i32, pi64, i32, dbl, i32, pi64, vp, vp, vp, vp, vp, vp, i32,
                                      ctypes.POINTER(nufft_opts), pd, pd]
     lib.nufft_tune_candidates.argtypes = [i32, i32, i32, ctypes.POINTER(i32), i32]
+    lib.nufft3_makeplan.argtypes = [i32, i32, dbl, i32, vp, ctypes.POINTER(nufft_opts), ctypes.POINTER(vp)]
+    lib.nufft3_setpts.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, vp]
+    lib.nufft3_execute.argtypes = [vp, vp, vp]
+    lib.nufft3_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(dbl), pi64, pd]
+    lib.nufft3_get_status.argtypes = [vp]
+    lib.nufft3_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -260,6 +267,52 @@ def nufft_batch_tune(type_: int, dim: int, nmodes, isign: int, eps: float, prec:
     return st, o, b.value, d.value
 
 
+def nufft3_makeplan(dim: int, isign: int, eps: float, prec: int, stream: int | None, opts: nufft_opts | None):
+    """Returns (status, type-3 plan handle)."""
+    h = ctypes.c_void_p()
+    st = _L().nufft3_makeplan(int(dim), int(isign), float(eps), int(prec), ctypes.c_void_p(stream or 0),
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return st, h
+
+
+def nufft3_setpts(plan, M: int, x: int, y: int, z: int, N: int, s: int, t: int, u: int) -> int:
+    v = lambda a: ctypes.c_void_p(a or 0)  # noqa: E731
+    return _L().nufft3_setpts(plan, int(M), v(x), v(y), v(z), int(N), v(s), v(t), v(u))
+
+
+def nufft3_execute(plan, c: int, f: int) -> int:
+    return _L().nufft3_execute(plan, ctypes.c_void_p(c or 0), ctypes.c_void_p(f or 0))
+
+
+def nufft3_plan_info(plan, dim: int):
+    w, beta = ctypes.c_int(), ctypes.c_double()
+    n = (ctypes.c_int64 * 3)()
+    g = (ctypes.c_double * 3)()
+    st = _L().nufft3_plan_info(plan, ctypes.byref(w), ctypes.byref(beta), n, g)
+    return st, dict(w=w.value, beta=beta.value, n=list(n)[:dim], gamma=list(g)[:dim])
+
+
+def nufft3_get_status(plan) -> int:
+    return _L().nufft3_get_status(plan)
+
+
+def nufft3_destroy(plan) -> int:
+    return _L().nufft3_destroy(plan)
+
+
+def _make_opts(opts: dict) -> nufft_opts:
+    o = nufft_default_opts()
+    for k, v in opts.items():
+        if k == "bin_size":
+            for i, b in enumerate(v):
+                o.bin_size[i] = int(b)
+        elif k == "upsampfac":
+            o.upsampfac = float(v)
+        else:
+            setattr(o, k, int(v))
+    return o
+
+
 def opts_dict(o: nufft_opts) -> dict:
     """The tunable fields of an options struct, as keyword arguments for Plan / BatchPlan."""
     return {"bin_size": tuple(o.bin_size), "max_subprob": o.max_subprob, "threads": o.threads,
@@ -413,6 +466,103 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             nufft_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan3:
+    """A type-3 plan (Eq. (3)) on one CUDA device, driven with torch tensors.
+
+    ``setpts(x, s)`` takes the sources x and target frequencies s as sequences
+    of dim coordinate arrays (M and N reals each); ``execute(c)`` with c of
+    shape (M,) returns f of shape (N,), f_k = sum_j c_j exp(i isign s_k.x_j).
+    CPU tensors are copied to the device and the result copied back.
+    """
+
+    def __init__(self, dim: int, eps: float = 1e-6, isign: int = 1, dtype=None, device=None, stream=None, **opts):
+        import torch
+        self._torch = torch
+        self.dim = int(dim)
+        self.isign = int(isign)
+        self.dtype = dtype if dtype is not None else torch.complex64
+        if self.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("dtype must be complex64 or complex128")
+        self.real_dtype = torch.float32 if self.dtype == torch.complex64 else torch.float64
+        self.prec = NUFFT_C64 if self.dtype == torch.complex64 else NUFFT_C128
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("Plan3 needs a CUDA device")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self._h = None
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            st, h = nufft3_makeplan(self.dim, self.isign, eps, self.prec, self.stream.cuda_stream, _make_opts(opts))
+            if st < 0:
+                raise NufftError(st, "nufft3_makeplan")
+            self.warning = st
+            self._h = h
+        self.M = self.N = None
+        self._keep = ()
+        self.info = None
+
+    def _dev(self, coords, what):
+        torch = self._torch
+        coords = list(coords)
+        if len(coords) != self.dim:
+            raise ValueError("need %d %s coordinate arrays" % (self.dim, what))
+        dev = [torch.as_tensor(v).to(device=self.device, dtype=self.real_dtype, non_blocking=True).contiguous()
+               for v in coords]
+        n = dev[0].numel()
+        if any(v.numel() != n for v in dev):
+            raise ValueError("%s coordinate arrays differ in length" % what)
+        return dev, n
+
+    def setpts(self, x, s):
+        torch = self._torch
+        xd, M = self._dev(x, "source")
+        sd, N = self._dev(s, "target")
+        px = [v.data_ptr() for v in xd] + [0] * (3 - self.dim)
+        ps = [v.data_ptr() for v in sd] + [0] * (3 - self.dim)
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft3_setpts(self._h, M, *px, N, *ps)
+        if st < 0:
+            raise NufftError(st, "nufft3_setpts")
+        self.M, self.N = M, N
+        self._keep = tuple(xd + sd)
+        self.info = nufft3_plan_info(self._h, self.dim)[1]
+        return self
+
+    def execute(self, c, out=None):
+        torch = self._torch
+        if self.M is None:
+            raise NufftError(-6, "Plan3.execute")
+        host = isinstance(c, torch.Tensor) and c.device.type == "cpu"
+        d = torch.as_tensor(c).to(device=self.device, dtype=self.dtype, non_blocking=True).contiguous()
+        if d.numel() != self.M:
+            raise ValueError("expected %d strengths" % self.M)
+        res = out if out is not None else torch.empty((self.N,), dtype=self.dtype, device=self.device)
+        if not res.is_contiguous() or res.device != self.device or res.dtype != self.dtype or res.numel() != self.N:
+            raise ValueError("out must be a contiguous %s tensor of %d values on %s" % (self.dtype, self.N,
+                                                                                        self.device))
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            st = nufft3_execute(self._h, d.data_ptr(), res.data_ptr())
+        if st < 0:
+            raise NufftError(st, "nufft3_execute")
+        self._keep_exec = (d,)
+        return res.to("cpu") if host else res
+
+    def status(self) -> int:
+        return nufft3_get_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            nufft3_destroy(self._h)
         self._h = None
 
     def __del__(self):

@@ -253,5 +253,8 @@ size_t plan_device_bytes(nufft_plan p);
 int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, int64_t mcap, size_t* bytes,
                         double sigma = 2.0);
 int plan_modes(nufft_plan p, int64_t* N, int* dim);
+void plan_choose_bins(Geom& g, bool dbl, const nufft_opts& o);  // bin extents for a grid (plan.cu's rule)
+void gl_positive_nodes(int p, double* q, double* wq);            // Gauss-Legendre rule of Eq. (quad)
+double sigma_from_opts(const nufft_opts& o);
 
 }  // namespace nufft

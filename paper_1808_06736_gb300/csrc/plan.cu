@@ -711,6 +711,19 @@ int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, in
   return NUFFT_OK;
 }
 
+void plan_choose_bins(Geom& g, bool dbl, const nufft_opts& o) { choose_bins(g, dbl, o); }
+
+void gl_positive_nodes(int p, double* q, double* wq) {
+  std::vector<double> a, b;
+  gauss_legendre_positive(p, a, b);
+  for (int i = 0; i < p; ++i) {
+    q[i] = a[(size_t)i];
+    wq[i] = b[(size_t)i];
+  }
+}
+
+double sigma_from_opts(const nufft_opts& o) { return sigma_of(o); }
+
 int plan_modes(nufft_plan p, int64_t* N, int* dim) {
   if (!p) return NUFFT_ERR_BAD_ARG;
   for (int i = 0; i < 3; ++i) N[i] = p->N[i];
