@@ -16,6 +16,10 @@ Two levels, both in IEEE double precision:
   Eq. (dft) with scipy's FFT, and the correction Eq. (pk) with the kernel
   transform from the Gauss-Legendre rule Eq. (quad).
 
+Also: the piecewise polynomial kernel of Sec. 5.3 (``piecewise_poly``,
+``piecewise_eval``) by the paper's own fitting method, and the type-3 sum and
+algorithm (``direct_type3``, ``type3``, Sec. 3.3).
+
 Readings of the paper that these functions fix (where it is silent or
 inconsistent):
 
@@ -236,6 +240,45 @@ def es_kernel(z, beta: float):
     m = np.abs(z) <= 1.0
     out[m] = np.exp(beta * (np.sqrt(1.0 - z[m] ** 2) - 1.0))
     return out
+
+
+def piecewise_poly(w: int, beta: float, p: int | None = None, kernel=None) -> np.ndarray:
+    """Sec. 5.3: the kernel psi on its support of w fine-grid cells is split into w unit
+    intervals, and on interval t (cell offsets tau in [t - w/2, t - w/2 + 1]) approximated by a
+    polynomial of degree p = w + 3 in the centred variable s = 2 (tau - (t - w/2)) - 1 in [-1, 1].
+    Monomial coefficients by a least-squares Vandermonde solve at collocation points on the
+    boundary of the square with corners +-1 +- i in the complex s-plane (the square tightly
+    enclosing the interval), with the kernel continued to complex arguments (principal square
+    root).  Returns a (w, p + 1) array, row t holding the coefficients of s^0 .. s^p.
+
+    ``kernel`` (a function of complex z = 2 tau / w) replaces the ES kernel, so the tests can
+    fit a function with a known polynomial form."""
+    p = w + 3 if p is None else int(p)
+    K = 2 * (p + 1)                                   # points per side
+    u = (np.arange(K) + 0.5) / K * 2.0 - 1.0
+    pts = np.concatenate([u - 1j, 1.0 + 1j * u, -u + 1j, -1.0 - 1j * u])
+    V = pts[:, None] ** np.arange(p + 1)
+    if kernel is None:
+        kernel = lambda z: np.exp(beta * (np.sqrt(1.0 - z * z + 0j) - 1.0))  # noqa: E731
+    C = np.empty((w, p + 1))
+    for t in range(w):
+        z = (t - w / 2.0 + 0.5 + 0.5 * pts) * (2.0 / w)
+        a = np.linalg.lstsq(V, kernel(z), rcond=None)[0]
+        C[t] = a.real
+    return C
+
+
+def piecewise_eval(C: np.ndarray, w: int, z) -> np.ndarray:
+    """The piecewise polynomial of ``piecewise_poly`` at real z in [-1, 1] (z = 2 tau / w), zero
+    outside: interval t = floor(tau + w/2), s = 2 (tau + w/2 - t) - 1, Horner's scheme."""
+    z = np.asarray(z, dtype=np.float64)
+    tau = z * (w / 2.0)
+    t = np.clip(np.floor(tau + w / 2.0).astype(np.int64), 0, w - 1)
+    s = 2.0 * (tau + w / 2.0 - t) - 1.0
+    y = np.zeros_like(z)
+    for m in range(C.shape[1] - 1, -1, -1):
+        y = y * s + C[t, m]
+    return np.where(np.abs(z) <= 1.0, y, 0.0)
 
 
 def gl_quadrature_nodes(w: int):

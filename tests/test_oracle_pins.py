@@ -441,3 +441,54 @@ def test_o2_type3_error_vs_truth(oracle_mod, d, M, N, eps):
     for isign in (1, -1):
         e = oracle_mod.rel_l2(oracle_mod.type3(xs, c, isign, ss, eps), oracle_mod.direct_type3(xs, c, isign, ss))
         assert eps / 100 < e <= 10 * eps, (isign, e)
+
+
+# ------------------------------------------------ piecewise polynomial kernel
+def _eps_of_width(oracle_mod, w, sigma):
+    """Smallest tolerance that the width rule maps to w (10^(1 - w) at sigma = 2)."""
+    if sigma == 2.0:
+        return 10.0 ** (1 - w)
+    return 10.0 ** (-(w - oracle_mod.SIGMA_54_OFFSET) / oracle_mod.eserr_slope(sigma))
+
+
+def test_piecewise_poly_reproduces_polynomials(oracle_mod):
+    """A kernel that is itself a polynomial of degree <= p is reproduced exactly (checks the
+    interval centres, the local variable and the Vandermonde solve); degree p + 2 is not."""
+    w = 7
+    p = w + 3
+    z = np.linspace(-1, 1, 1001)
+    for deg, exact in ((p, True), (p - 4, True), (p + 2, False)):
+        coef = np.random.default_rng(deg).standard_normal(deg + 1)
+        poly = lambda v, c=coef: np.polynomial.polynomial.polyval(v, c)  # noqa: E731
+        C = oracle_mod.piecewise_poly(w, 0.0, kernel=poly)
+        err = np.abs(oracle_mod.piecewise_eval(C, w, z) - poly(z)).max()
+        if exact:
+            assert err < 1e-11, (deg, err)
+        else:
+            assert err > 1e-8, (deg, err)
+
+
+@pytest.mark.parametrize("sigma", [2.0, 1.25])
+def test_piecewise_poly_error_small_against_eps(oracle_mod, sigma):
+    """Sec. 5.3: with p = w + 3 the approximation error is small relative to the tolerance that
+    selects w: max |poly - ES| <= eps / 2 (floor 1e-14, double rounding), every w = 2..16."""
+    z = np.linspace(-1, 1, 4001)
+    for w in range(2, 17):
+        beta = oracle_mod.es_beta(w, sigma)
+        C = oracle_mod.piecewise_poly(w, beta)
+        err = np.abs(oracle_mod.piecewise_eval(C, w, z) - oracle_mod.es_kernel(z, beta)).max()
+        assert err <= max(0.5 * _eps_of_width(oracle_mod, w, sigma), 1e-14), (w, err)
+
+
+def test_piecewise_poly_planted_mistakes(oracle_mod):
+    """The error pin catches a reversed local variable and coefficients of the wrong interval."""
+    w, sigma = 6, 2.0
+    beta = oracle_mod.es_beta(w, sigma)
+    z = np.linspace(-1, 1, 2001)
+    C = oracle_mod.piecewise_poly(w, beta)
+    ref = oracle_mod.es_kernel(z, beta)
+    bound = 0.5 * _eps_of_width(oracle_mod, w, sigma)
+    flipped = C * ((-1.0) ** np.arange(C.shape[1]))      # s -> -s
+    rolled = np.roll(C, 1, axis=0)                         # interval t uses t - 1's polynomial
+    for bad in (flipped, rolled):
+        assert np.abs(oracle_mod.piecewise_eval(bad, w, z) - ref).max() > 100 * bound
