@@ -74,13 +74,16 @@ def parse():
     ap.add_argument("--kind", default="uniform", choices=["uniform", "clustered"])
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"],
                     help="c64 (the headline: complex64, float arithmetic) or c128 (complex128, double)")
+    ap.add_argument("--kerevalmeth", type=int, default=0, choices=[0, 1],
+                    help="kernel evaluation: 0 the ES formula, 1 the piecewise polynomial of Sec. 5.3")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=300_000)
-    ap.add_argument("--workload", default="3d", choices=["3d", "batched2d", "serving"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "batched2d", "serving", "type3"],
                     help="3d: the 3D type-1/type-2 workload (default); batched2d: many uneven 2D type-2 "
                          "transforms, batched plan against one plan per transform; serving: a Poisson stream "
-                         "of mixed requests through the request loop against the plain plan path")
+                         "of mixed requests through the request loop against the plain plan path; type3: "
+                         "3D type 3 with 1e7 sources and 1e7 target frequencies on a 256^3 grid")
     ap.add_argument("--B", type=int, default=1024, help="transforms in the batched2d workload")
     ap.add_argument("--requests", type=int, default=2000, help="requests in the serving trace")
     ap.add_argument("--rate", type=float, default=2000.0, help="mean arrivals per second in the serving trace")
@@ -193,8 +196,8 @@ def run_cuda(args, ws, rank, local):
     c = I.torch_complex_normal(seed + 1, M, dev, cdt)
     f = I.torch_complex_normal(seed + 2, N ** d, dev, cdt)
     stream = torch.cuda.current_stream(dev)
-    p1 = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=cdt, device=dev, debug=1)
-    p2 = pkg.Plan(2, Ns, eps=eps, isign=-1, dtype=cdt, device=dev, debug=1)
+    p1 = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=cdt, device=dev, debug=1, kerevalmeth=args.kerevalmeth)
+    p2 = pkg.Plan(2, Ns, eps=eps, isign=-1, dtype=cdt, device=dev, debug=1, kerevalmeth=args.kerevalmeth)
     fout = torch.empty((1,) + tuple(Ns), dtype=cdt, device=dev)
     cout = torch.empty((1, M), dtype=cdt, device=dev)
     slots = {k: [] for k in ("fold", "scan", "scatter", "spread", "fft1", "deconv", "precorrect", "fft2",
@@ -507,6 +510,76 @@ def run_batched2d(args):
     return 0
 
 
+def run_type3(args):
+    """Type 3 (Eq. (3), Sec. 3.3), 3D, complex64, eps = 1e-5: M = N = 1e7 sources and target
+    frequencies, uniform in boxes centred at (1, 2, 3) +- 10 and (-5, 4, 7) +- 19.6, so that the
+    space-bandwidth product gives a 256^3 fine grid (n = 2 sigma X S / pi + w).  One step =
+    setpts (bounding boxes, binning, target factors, inner type-2 setpts) + execute."""
+    import torch
+
+    import nufft_inputs as I
+    import paper_1808_06736_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    M = N = 10_000_000
+    X, S = 10.0, 19.6
+    g = torch.Generator(device=dev)
+    g.manual_seed(9100)
+    xs = [(torch.rand(M, generator=g, device=dev, dtype=torch.float64) * 2 - 1) * X + c0 for c0 in (1.0, 2.0, 3.0)]
+    ss = [(torch.rand(N, generator=g, device=dev, dtype=torch.float64) * 2 - 1) * S + c0 for c0 in (-5.0, 4.0, 7.0)]
+    xs = [v.float() for v in xs]
+    ss = [v.float() for v in ss]
+    c = I.torch_complex_normal(9101, M, dev, torch.complex64)
+    out = torch.empty(N, dtype=torch.complex64, device=dev)
+    p = pkg.Plan3(3, eps=args.eps, isign=1, dtype=torch.complex64, device=dev, kerevalmeth=args.kerevalmeth)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step():
+        p.setpts(xs, ss)
+        p.execute(c, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    split = []
+    for _ in range(3):
+        ev[0].record(stream)
+        p.setpts(xs, ss)
+        ev[1].record(stream)
+        p.execute(c, out=out)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        split.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    assert p.status() == 0
+    info = dict(p.info)
+    p.close()
+    line = {"metric": "type-3 NU points/s ((M + N) / step, 3D, eps=%g, fp32)" % args.eps,
+            "value": (M + N) / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "type3", "M": M, "N": N, "source_box": "(1,2,3) +- 10",
+                       "target_box": "(-5,4,7) +- 19.6", "fine_grid": info["n"], "gamma": info["gamma"],
+                       "w": info["w"], "step": "setpts + execute",
+                       "kernel_eval": "piecewise polynomial" if args.kerevalmeth == 1 else "ES formula"},
+            "setpts_ms": statistics.median(v[0] for v in split),
+            "execute_ms": statistics.median(v[1] for v in split), "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def _pct(v, q):
     v = sorted(v)
     if not v:
@@ -674,6 +747,7 @@ def config_dict(args):
             "modes": [args.N] * 3, "fine_grid": [2 * args.N] * 3, "M": args.M, "points": args.kind,
             "eps": args.eps, "step": "setpts+type1 and setpts+type2 on the same points; value = 2M/step",
             "l2": "inputs larger than L2 (1.2 GB coordinates, 1 GB fine grids), no flush",
+            "kernel_eval": "piecewise polynomial (Sec. 5.3)" if args.kerevalmeth == 1 else "ES formula",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -684,6 +758,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched2d":
         return run_batched2d(args)
+    if args.workload == "type3":
+        return run_type3(args)
     if args.workload == "serving":
         return run_serving_line(args)
     r = run_cuda(args, ws, rank, local)

@@ -71,7 +71,11 @@ typedef struct {
   int threads;        /* threads per block of the spread / interp kernels (0: choose) */
   int sparse_max;     /* subproblems of at most this many points (<= 32) run one per warp straight
                          on the fine grid instead of through a shared-memory tile (0: 32, -1: never) */
-  int reserved[7];    /* set to zero */
+  int kerevalmeth;    /* kernel evaluation in the spread / interp kernels: 0 the ES formula (one exp and one
+                         sqrt per node), 1 the piecewise polynomial of Sec. 5.3 (w intervals of degree
+                         w + 3, Horner's scheme; see nufft_horner_coeffs).  The complex128 interpolation
+                         (double-float) and the gradient kernels always use the formula. */
+  int reserved[6];    /* set to zero */
   double upsampfac;   /* fine grid / modes per dimension, sigma: 2 (0 means 2) or 1.25 (smaller FFTs and
                          grids, wider kernel: w from the slope of Eq. (ESerr), beta from Eq. (gam); more
                          rounding amplification, see nufft_choose_params_sigma) */
@@ -208,6 +212,15 @@ int nufft_correction_factors(int64_t N, int64_t n, int w, double beta, double* o
 
 /* Smallest 2^a 3^b 5^c >= m (m >= 1); returns -1 on overflow or m < 1. */
 int64_t nufft_next235(int64_t m);
+
+/* Host-only: the piecewise polynomial of Sec. 5.3 used with opts.kerevalmeth = 1.  The kernel
+ * psi(tau) = phi(2 tau / w) on its support tau in [-w/2, w/2] (fine-grid cells) is split into
+ * w unit intervals; on interval t (tau in [t - w/2, t - w/2 + 1]) it is the polynomial
+ * sum_m out[t (w + 4) + m] s^m of degree w + 3 in s = 2 (tau - t + w/2) - 1 in [-1, 1].
+ * Coefficients by interpolation at the w + 4 Chebyshev points of the first kind, converted to
+ * monomials.  out: w (w + 4) doubles.  Returns NUFFT_OK or NUFFT_ERR_BAD_ARG (w outside
+ * [2, 16], beta <= 0, out NULL). */
+int nufft_horner_coeffs(int w, double beta, double* out);
 
 /* ------------------------------------------------------------------ batches
  * Many independent transforms in one plan: B transforms of one type,

@@ -19,6 +19,7 @@ __all__ = [
     "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
     "nufft_execute", "nufft_execute_grad", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
     "nufft_strerror", "nufft_choose_params", "nufft_choose_params_sigma", "nufft_correction_factors", "nufft_next235",
+    "nufft_horner_coeffs",
     "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
     "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy", "nufft_tune", "nufft_batch_tune",
     "nufft_tune_candidates", "opts_dict", "tune_plan", "tune_batch", "Plan3", "nufft3_makeplan", "nufft3_setpts",
@@ -44,7 +45,8 @@ class NufftError(RuntimeError):
 class nufft_opts(ctypes.Structure):
     _fields_ = [("debug", ctypes.c_int), ("chkbnds", ctypes.c_int), ("modeord", ctypes.c_int),
                 ("bin_size", ctypes.c_int * 3), ("max_subprob", ctypes.c_int), ("threads", ctypes.c_int),
-                ("sparse_max", ctypes.c_int), ("reserved", ctypes.c_int * 7), ("upsampfac", ctypes.c_double)]
+                ("sparse_max", ctypes.c_int), ("kerevalmeth", ctypes.c_int), ("reserved", ctypes.c_int * 6),
+                ("upsampfac", ctypes.c_double)]
 
 
 _lib = None
@@ -82,6 +84,7 @@ def _L():
                                               pi64]
     lib.nufft_correction_factors.argtypes = [i64, i64, i32, dbl, ctypes.POINTER(ctypes.c_double)]
     lib.nufft_next235.argtypes = [i64]
+    lib.nufft_horner_coeffs.argtypes = [i32, dbl, ctypes.POINTER(ctypes.c_double)]
     lib.nufft_next235.restype = i64
     lib.nufft_spread_noalloc.argtypes = [i32, pi64, i32, dbl, i64, vp, vp, vp, vp, vp, vp]
     lib.nufft_batch_makeplan.argtypes = [i32, i32, i32, pi64, i32, dbl, i32, vp, ctypes.POINTER(nufft_opts),
@@ -184,6 +187,16 @@ def nufft_correction_factors(N: int, n: int, w: int, beta: float):
     out = (ctypes.c_double * int(N))()
     st = _L().nufft_correction_factors(int(N), int(n), int(w), float(beta), out)
     return st, list(out)
+
+
+def nufft_horner_coeffs(w: int, beta: float):
+    """(status, w x (w + 4) nested list of the Sec. 5.3 polynomial coefficients)."""
+    buf = (ctypes.c_double * (w * (w + 4)))() if 2 <= w <= 16 else None
+    st = _L().nufft_horner_coeffs(int(w), float(beta), buf)
+    if st != 0:
+        return st, None
+    v = list(buf)
+    return st, [v[t * (w + 4):(t + 1) * (w + 4)] for t in range(w)]
 
 
 def nufft_next235(m: int) -> int:
@@ -316,7 +329,7 @@ def _make_opts(opts: dict) -> nufft_opts:
 def opts_dict(o: nufft_opts) -> dict:
     """The tunable fields of an options struct, as keyword arguments for Plan / BatchPlan."""
     return {"bin_size": tuple(o.bin_size), "max_subprob": o.max_subprob, "threads": o.threads,
-            "sparse_max": o.sparse_max, "upsampfac": o.upsampfac}
+            "sparse_max": o.sparse_max, "kerevalmeth": o.kerevalmeth, "upsampfac": o.upsampfac}
 
 
 # --------------------------------------------------------------- torch layer

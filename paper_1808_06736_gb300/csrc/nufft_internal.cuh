@@ -28,6 +28,7 @@ struct Geom {
   int ntile;     // T[0] T[1] T[2]
   int maxsub;    // most points in one subproblem
   int sparse_max;  // subproblems with at most this many points take the per-warp path (0: none)
+  int horner;      // 1: kernel values from the piecewise polynomial of Sec. 5.3 (horner_table)
 };
 
 // Bin ids run over super-blocks of sb[0] x sb[1] x sb[2] bins, dimension 1
@@ -256,5 +257,8 @@ int plan_modes(nufft_plan p, int64_t* N, int* dim);
 void plan_choose_bins(Geom& g, bool dbl, const nufft_opts& o);  // bin extents for a grid (plan.cu's rule)
 void gl_positive_nodes(int p, double* q, double* wq);            // Gauss-Legendre rule of Eq. (quad)
 double sigma_from_opts(const nufft_opts& o);
+// w x (w + 4) monomial coefficients of Sec. 5.3's piecewise polynomial (see nufft_horner_coeffs);
+// computed once per (w, beta) and kept for the life of the process
+const double* horner_table(int w, double beta);
 
 }  // namespace nufft

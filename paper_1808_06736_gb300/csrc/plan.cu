@@ -14,7 +14,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "nufft_internal.cuh"
@@ -374,6 +377,13 @@ int nufft_choose_params_sigma(int dim, const int64_t* nmodes, double eps, int pr
   return choose_params_impl(dim, nmodes, eps, prec, w, beta, n, sigma);
 }
 
+int nufft_horner_coeffs(int w, double beta, double* out) {
+  if (w < 2 || w > 16 || !(beta > 0.0) || !out) return NUFFT_ERR_BAD_ARG;
+  const double* a = nufft::horner_table(w, beta);
+  std::memcpy(out, a, sizeof(double) * (size_t)w * (size_t)(w + 4));
+  return NUFFT_OK;
+}
+
 int nufft_correction_factors(int64_t N, int64_t n, int w, double beta, double* out) {
   return correction_impl(N, n, w, beta, out);
 }
@@ -438,9 +448,11 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   for (int i = 0; i < 3; ++i) g.n[i] = (int)n[i];
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
   g.sparse_max = sparse_max_of(p->opts);
+  g.horner = p->opts.kerevalmeth == 1 ? 1 : 0;
   choose_bins(g, p->dbl, p->opts);
   int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-  if (threads % 32 != 0 || threads > 256) return fail(p, NUFFT_ERR_BAD_ARG);
+  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1)
+    return fail(p, NUFFT_ERR_BAD_ARG);
 
   // device buffers owned by the plan
   if (dev_alloc(&p->grid, p->ngrid * p->csize) != cudaSuccess) return fail(p, NUFFT_ERR_ALLOC);
@@ -698,6 +710,7 @@ int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, in
   for (int i = 0; i < 3; ++i) g.n[i] = (int)n[i];
   g.maxsub = dbl ? 512 : 1024;
   g.sparse_max = 32;
+  g.horner = 0;
   nufft_opts o;
   nufft_default_opts(&o);
   choose_bins(g, dbl, o);
@@ -712,6 +725,61 @@ int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, in
 }
 
 void plan_choose_bins(Geom& g, bool dbl, const nufft_opts& o) { choose_bins(g, dbl, o); }
+
+// Sec. 5.3's piecewise polynomial: on interval t the kernel psi(tau) = phi(2 tau / w),
+// tau = t - w/2 + (s + 1)/2, as a polynomial of degree P - 1 = w + 3 in s.  Interpolation at
+// the P Chebyshev points of the first kind gives the Chebyshev coefficients
+//   c_j = (2 - [j = 0]) / P * sum_k psi(s_k) T_j(s_k),  s_k = cos(pi (k + 1/2) / P),
+// and the recurrence T_{j+1} = 2 s T_j - T_{j-1} turns them into monomial coefficients.
+// The kernel is analytic on every interval (its square-root branch points sit at the ends of
+// the support, where phi = e^-beta), so the monomial form stays well conditioned: the sum of
+// |coefficients| of an interval is about 1.
+static void horner_fit(int w, double beta, double* out) {
+  const int P = w + 4;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> f((size_t)P), c((size_t)P), tm((size_t)P), tj((size_t)P), tn((size_t)P);
+  for (int t = 0; t < w; ++t) {
+    for (int k = 0; k < P; ++k) {
+      const double sk = std::cos(pi * (k + 0.5) / P);
+      const double z = (t - 0.5 * w + 0.5 * (sk + 1.0)) * 2.0 / w;
+      f[(size_t)k] = std::fabs(z) <= 1.0 ? std::exp(beta * (std::sqrt(std::max(1.0 - z * z, 0.0)) - 1.0)) : 0.0;
+    }
+    for (int j = 0; j < P; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < P; ++k) acc += f[(size_t)k] * std::cos(pi * j * (k + 0.5) / P);
+      c[(size_t)j] = acc * (j == 0 ? 1.0 : 2.0) / P;
+    }
+    double* a = out + (size_t)t * P;
+    for (int m = 0; m < P; ++m) a[m] = 0.0;
+    std::fill(tm.begin(), tm.end(), 0.0);  // T_{j-1}
+    std::fill(tj.begin(), tj.end(), 0.0);  // T_j
+    tj[0] = 1.0;
+    for (int j = 0; j < P; ++j) {
+      for (int m = 0; m < P; ++m) a[m] += c[(size_t)j] * tj[(size_t)m];
+      if (j + 1 == P) break;
+      for (int m = 0; m < P; ++m) {
+        const double up = m > 0 ? tj[(size_t)m - 1] : 0.0;
+        tn[(size_t)m] = (j == 0 ? 1.0 : 2.0) * up - (j == 0 ? 0.0 : tm[(size_t)m]);
+      }
+      tm = tj;
+      tj = tn;
+    }
+  }
+}
+
+const double* horner_table(int w, double beta) {
+  static std::mutex mu;
+  static std::map<std::pair<int, double>, std::vector<double>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(w, beta);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    std::vector<double> a((size_t)w * (size_t)(w + 4));
+    horner_fit(w, beta, a.data());
+    it = cache.emplace(key, std::move(a)).first;
+  }
+  return it->second.data();
+}
 
 void gl_positive_nodes(int p, double* q, double* wq) {
   std::vector<double> a, b;
@@ -953,6 +1021,7 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   g.half = p->w / 2;
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
   g.sparse_max = sparse_max_of(p->opts);
+  g.horner = p->opts.kerevalmeth == 1 ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
     int64_t mx = 1;
     for (int t = 0; t < B; ++t) mx = std::max(mx, n[(size_t)t * 3 + i]);
@@ -1068,7 +1137,8 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   okc &= cudaMemset(p->small, 0, sizeof(int) * 4) == cudaSuccess;
   if (!okc) return batch_fail(p, NUFFT_ERR_CUDA);
   int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-  if (threads % 32 != 0 || threads > 256) return batch_fail(p, NUFFT_ERR_BAD_ARG);
+  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1)
+    return batch_fail(p, NUFFT_ERR_BAD_ARG);
   cudaError_t e = (type == 1) ? spread_config(p->dbl, g, threads, &p->cfg) : interp_config(p->dbl, g, threads, &p->cfg);
   if (e != cudaSuccess) return batch_fail(p, NUFFT_ERR_CUDA);
   for (auto& c : p->classes) {

@@ -84,6 +84,60 @@ __device__ __forceinline__ T node_z(int t, int step, T f) {
   return (T(t - W / 2 + step) - f) * (T(2) / T(W));
 }
 
+// Kernel evaluation of a launch: the ES exponent factor kpar and, with horner
+// set, the piecewise polynomial of Sec. 5.3 (w intervals, degree w + 3,
+// a[t * NC + m] the coefficient of s^m on interval t).  Kernels take it as a
+// __grid_constant__ parameter, so in the unrolled Horner loops each coefficient
+// is a constant-bank operand of its FMA.
+template <typename T, int W>
+struct KEval {
+  static constexpr int NC = W + 4;
+  T kpar;
+  int horner;
+  T a[W * NC];
+};
+
+// Node t of a coordinate with fraction f and stencil step lies at
+// tau = t - floor(w/2) + step - f cells, in the unit interval t of the support
+// [-w/2, w/2]; its local variable is s = 2 (tau - t + w/2) - 1.
+template <int W, typename T>
+__device__ __forceinline__ T horner_s(int step, T f) {
+  return T(2) * (T(step) - f) + T((W & 1) ? 0 : -1);
+}
+
+// kernel value of one node (t not known at compile time)
+template <typename T, int W>
+__device__ __forceinline__ T kernel_node(const KEval<T, W>& ke, int t, int step, T f) {
+  if (ke.horner) {
+    constexpr int NC = KEval<T, W>::NC;
+    const T x = horner_s<W>(step, f);
+    const T* a = ke.a + t * NC;
+    T y = a[NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) y = fma(y, x, a[m]);
+    return y;
+  }
+  return es_eval(node_z<W>(t, step, f), ke.kpar);
+}
+
+// kernel values of all W nodes of a coordinate
+template <typename T, int W>
+__device__ __forceinline__ void kernel_row(const KEval<T, W>& ke, int step, T f, T* k) {
+  if (ke.horner) {
+    constexpr int NC = KEval<T, W>::NC;
+    const T x = horner_s<W>(step, f);
+#pragma unroll
+    for (int t = 0; t < W; ++t) k[t] = ke.a[t * NC + NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m)
+#pragma unroll
+      for (int t = 0; t < W; ++t) k[t] = fma(k[t], x, ke.a[t * NC + m]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, step, f), ke.kpar);
+  }
+}
+
 // L2 eviction-priority policies: fine-grid lines that neighbouring tiles will
 // touch again are kept (evict_last); strengths gathered once per point and
 // results scattered once are let go first (evict_first).
@@ -228,13 +282,12 @@ __device__ __forceinline__ void bucket_order(int cnt, Stage<T, D>& st, const int
 
 // Per-point kernel values along one dimension.
 template <typename T, int W>
-__device__ __forceinline__ void point_weights(T v, int B, T kpar, int& ts, T* k) {
+__device__ __forceinline__ void point_weights(T v, int B, const KEval<T, W>& ke, int& ts, T* k) {
   int il = min((int)v, B - 1);
   T f = v - T(il);
   int s = stencil_step<W>(f);
   ts = il + s;
-#pragma unroll
-  for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, s, f), kpar);
+  kernel_row<T, W>(ke, s, f, k);
 }
 
 // Add a fixed-point tile (scaled by inv) into the fine grid with periodic
@@ -320,7 +373,7 @@ __device__ __forceinline__ void next_subproblem(const Geom& g, const Sorted& s, 
 }
 
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T kpar, Sorted s,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, const __grid_constant__ KEval<T, W> ke, Sorted s,
                                                 const typename Traits<T>::C* __restrict__ c,
                                                 typename Traits<T>::C* __restrict__ grid,
                                                 int* __restrict__ work, BatchTable bt) {
@@ -411,11 +464,11 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T k
       const Rec rq = rec[p0 + q];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights<T, W>(rq.v[0], g.B[0], kpar, ts0, k0);
+      point_weights<T, W>(rq.v[0], g.B[0], ke, ts0, k0);
       T k1[(D > 1) ? W : 1];
       T f2 = T(0);
       int st2 = 0;
-      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], kpar, ts1, k1);
+      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], ke, ts1, k1);
       else k1[0] = T(1);
       if constexpr (D > 2) {
         T v2 = rq.v[2];
@@ -432,7 +485,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T k
 #pragma unroll 1
       for (int l2 = 0; l2 < W2; ++l2) {
         T k2 = T(1);
-        if constexpr (D > 2) k2 = es_eval(node_z<W>(l2, st2, f2), kpar);
+        if constexpr (D > 2) k2 = kernel_node<T, W>(ke, l2, st2, f2);
         const T cr2 = cr * k2, ci2 = ci * k2;
 #pragma unroll
         for (int l1 = 0; l1 < W1; ++l1) {
@@ -460,7 +513,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, T k
 
 // ----------------------------------------------------------------- interp
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T kpar, Sorted s,
+__global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, const __grid_constant__ KEval<T, W> ke, Sorted s,
                                                 const typename Traits<T>::C* __restrict__ grid,
                                                 typename Traits<T>::C* __restrict__ c,
                                                 int* __restrict__ work, BatchTable bt) {
@@ -523,11 +576,11 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T k
       const Rec rq = rec[p0 + q];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights<T, W>(rq.v[0], g.B[0], kpar, ts0, k0);
+      point_weights<T, W>(rq.v[0], g.B[0], ke, ts0, k0);
       T k1[(D > 1) ? W : 1];
       T f2 = T(0);
       int st2 = 0;
-      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], kpar, ts1, k1);
+      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], ke, ts1, k1);
       else k1[0] = T(1);
       if constexpr (D > 2) {
         T v2 = rq.v[2];
@@ -557,7 +610,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, T k
           bi = fma(si, k1[l1], bi);
         }
         T k2 = T(1);
-        if constexpr (D > 2) k2 = es_eval(node_z<W>(l2, st2, f2), kpar);
+        if constexpr (D > 2) k2 = kernel_node<T, W>(ke, l2, st2, f2);
         ar = fma(br, k2, ar);
         ai = fma(bi, k2, ai);
       }
@@ -597,7 +650,7 @@ __device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int& 
 }
 
 template <int D, int W>
-__global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, double kpar, Sorted s, const double2* __restrict__ grid,
+__global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_constant__ KEval<double, W> ke, Sorted s, const double2* __restrict__ grid,
                                                       double2* __restrict__ c, int* __restrict__ work, BatchTable bt) {
   using Rec = typename Traits<double>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -612,7 +665,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, double kpar, Sorte
   Stage<double, D> st = carve_stage<double, D>(reinterpret_cast<unsigned char*>(tile + ntile), maxsub);
   const Rec* __restrict__ rec = reinterpret_cast<const Rec*>(s.rec);
   const int T0 = g.T[0], T01 = g.T[0] * g.T[1];
-  const DF bdf = df_of(kpar);  // beta
+  const DF bdf = df_of(ke.kpar);  // beta (the double-float path evaluates the ES formula)
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -765,8 +818,8 @@ __device__ __forceinline__ void sparse_geometry(const Geom& g, const BatchTable&
 // Weights of the points jb .. jb+PP-1 (records held by lanes jb + p) into wb,
 // entry p*W*D + d*W + t.  Every lane takes part in the shuffles.
 template <typename T, int D, int W>
-__device__ __forceinline__ void sparse_weights(const typename Traits<T>::Rec& r, int jb, const Geom& gg, T kpar,
-                                               T* wb) {
+__device__ __forceinline__ void sparse_weights(const typename Traits<T>::Rec& r, int jb, const Geom& gg,
+                                               const KEval<T, W>& ke, T* wb) {
   using S = Sparse<W, D>;
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -781,7 +834,7 @@ __device__ __forceinline__ void sparse_weights(const typename Traits<T>::Rec& r,
       const T v = dd == 0 ? v0 : (dd == 1 ? v1 : v2);
       const int il = min((int)v, gg.B[dd] - 1);
       const T f = v - T(il);
-      wb[e] = es_eval(node_z<W>(t, stencil_step<W>(f), f), kpar);
+      wb[e] = kernel_node<T, W>(ke, t, stencil_step<W>(f), f);
     }
   }
   __syncwarp();
@@ -808,7 +861,7 @@ __device__ __forceinline__ long long sparse_cell(const T* v, const int* org, con
 }
 
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_spread_sparse(Geom g, T kpar, Sorted s,
+__global__ void __launch_bounds__(256) k_spread_sparse(Geom g, const __grid_constant__ KEval<T, W> ke, Sorted s,
                                                        const typename Traits<T>::C* __restrict__ c,
                                                        typename Traits<T>::C* __restrict__ grid, BatchTable bt) {
   using C = typename Traits<T>::C;
@@ -838,7 +891,7 @@ __global__ void __launch_bounds__(256) k_spread_sparse(Geom g, T kpar, Sorted s,
     }
     C* gt = grid + goff;
     for (int jb = 0; jb < cnt; jb += S::PP) {
-      sparse_weights<T, D, W>(r, jb, gg, kpar, wb);
+      sparse_weights<T, D, W>(r, jb, gg, ke, wb);
       if (S::PP > 1) {
         const int p = lane / S::CP, cell = lane - p * S::CP;
         const int src = (jb + p) & 31;
@@ -868,7 +921,7 @@ __global__ void __launch_bounds__(256) k_spread_sparse(Geom g, T kpar, Sorted s,
 }
 
 template <typename T, int D, int W>
-__global__ void __launch_bounds__(256) k_interp_sparse(Geom g, T kpar, Sorted s,
+__global__ void __launch_bounds__(256) k_interp_sparse(Geom g, const __grid_constant__ KEval<T, W> ke, Sorted s,
                                                        const typename Traits<T>::C* __restrict__ grid,
                                                        typename Traits<T>::C* __restrict__ c, BatchTable bt) {
   using C = typename Traits<T>::C;
@@ -895,7 +948,7 @@ __global__ void __launch_bounds__(256) k_interp_sparse(Geom g, T kpar, Sorted s,
     if (lane < cnt) r = rec[p0 + lane];
     const C* gt = grid + goff;
     for (int jb = 0; jb < cnt; jb += S::PP) {
-      sparse_weights<T, D, W>(r, jb, gg, kpar, wb);
+      sparse_weights<T, D, W>(r, jb, gg, ke, wb);
       if (S::PP > 1) {
         const int p = lane / S::CP, cell = lane - p * S::CP;
         const int src = (jb + p) & 31;
@@ -976,6 +1029,17 @@ inline double kernel_param<double>(double beta) {
   return beta;
 }
 
+// the launch's kernel evaluation parameters (the table for g.horner)
+template <typename T, int W>
+inline KEval<T, W> make_keval(const Geom& g, double beta) {
+  KEval<T, W> ke;
+  ke.kpar = kernel_param<T>(beta);
+  ke.horner = g.horner ? 1 : 0;
+  const double* a = g.horner ? horner_table(W, beta) : nullptr;
+  for (int i = 0; i < W * KEval<T, W>::NC; ++i) ke.a[i] = a ? T(a[i]) : T(0);
+  return ke;
+}
+
 template <typename T, int D, int W>
 cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* c, void* grid,
                        int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
@@ -991,12 +1055,12 @@ cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* 
     return cudaSuccess;
   }
   kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
-      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
+      g, make_keval<T, W>(g, beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
       reinterpret_cast<typename Traits<T>::C*>(grid), work, bt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || g.sparse_max <= 0) return e;
   k_spread_sparse<T, D, W><<<2 * cfg.blocks, 256, 0, st>>>(
-      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
+      g, make_keval<T, W>(g, beta), s, reinterpret_cast<const typename Traits<T>::C*>(c),
       reinterpret_cast<typename Traits<T>::C*>(grid), bt);
   return cudaGetLastError();
 }
@@ -1016,12 +1080,12 @@ cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* 
     return cudaSuccess;
   }
   kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
-      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
+      g, make_keval<T, W>(g, beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
       reinterpret_cast<typename Traits<T>::C*>(c), work, bt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || g.sparse_max <= 0) return e;
   k_interp_sparse<T, D, W><<<2 * cfg.blocks, 256, 0, st>>>(
-      g, kernel_param<T>(beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
+      g, make_keval<T, W>(g, beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
       reinterpret_cast<typename Traits<T>::C*>(c), bt);
   return cudaGetLastError();
 }

@@ -3,10 +3,12 @@
 // shared-memory tile, bin + w per dimension), the largest subproblem, the
 // threads per block, the threshold below which a subproblem runs one per
 // warp (the per-warp path's lanes cooperate on a point's stencil, the tiled
-// path gives each thread its own points) and the upsampling factor (2, or
-// 5/4 where eps allows: a grid about 4x smaller in 3D for a wider kernel).
-// The search is staged: bin shapes first, then the subproblem size, the
-// sparse threshold, the block size and the upsampling factor, each stage
+// path gives each thread its own points), the kernel evaluation (the ES
+// formula or the piecewise polynomial of Sec. 5.3) and the upsampling factor
+// (2, or 5/4 where eps allows: a grid about 4x smaller in 3D for a wider
+// kernel).  The search is staged: bin shapes first, then the subproblem size,
+// the sparse threshold, the block size, the kernel evaluation and the
+// upsampling factor, each stage
 // starting from the best configuration so far.  The default configuration is
 // always timed first, so the result is never slower than it as measured.
 #include <cuda_runtime.h>
@@ -124,6 +126,11 @@ int search(int dim, bool dbl, int w, bool try_sigma54, Trial& t, cudaStream_t st
   {
     nufft_opts o = cur;
     o.threads = 128;
+    consider(o);
+  }
+  {  // Sec. 5.3's piecewise polynomial instead of exp and sqrt per kernel value
+    nufft_opts o = cur;
+    o.kerevalmeth = 1;
     consider(o);
   }
   if (try_sigma54) {  // smaller grids and FFTs for a wider kernel; its own default bins

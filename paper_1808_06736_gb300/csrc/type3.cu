@@ -278,9 +278,11 @@ int setpts_t(nufft_plan3 p, int64_t M, const void* x, const void* y, const void*
   for (int i = 0; i < 3; ++i) g.n[i] = (int)p->n[i];
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
   g.sparse_max = p->opts.sparse_max < 0 ? 0 : (p->opts.sparse_max == 0 ? 32 : std::min(p->opts.sparse_max, 32));
+  g.horner = p->opts.kerevalmeth == 1 ? 1 : 0;
   plan_choose_bins(g, p->dbl, p->opts);
   const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-  if (threads % 32 != 0 || threads > 256) return NUFFT_ERR_BAD_ARG;
+  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1)
+    return NUFFT_ERR_BAD_ARG;
   if (spread_config(p->dbl, g, threads, &p->scfg) != cudaSuccess) return NUFFT_ERR_CUDA;
   if (!ensure(p->gridcap, ngrid, {{&p->grid, p->cs}})) return NUFFT_ERR_ALLOC;
   const int nrep = replicas_for(g.nbins);

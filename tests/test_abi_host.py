@@ -23,7 +23,7 @@ def lib():
 def _declared():
     text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(nufft_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(nufft[0-9]*_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -130,3 +130,35 @@ def test_choose_params_sigma54_matches_oracle(lib, oracle_mod):
     st, w, _, _ = lib.nufft_choose_params_sigma(1, [100], 1e-11, lib.NUFFT_C128, 1.25)
     assert st == 1 and w == 16
     assert lib.nufft_choose_params_sigma(1, [100], 1e-5, lib.NUFFT_C64, 1.5)[0] == -1
+
+
+def _eps_of_width(oracle_mod, w, sigma):
+    if sigma == 2.0:
+        return 10.0 ** (1 - w)
+    return 10.0 ** (-(w - oracle_mod.SIGMA_54_OFFSET) / oracle_mod.eserr_slope(sigma))
+
+
+@pytest.mark.parametrize("sigma", [2.0, 1.25])
+def test_horner_coeffs_against_kernel_and_oracle(lib, oracle_mod, sigma):
+    """The library's Sec. 5.3 table (Chebyshev interpolation) against the ES kernel: max error
+    <= eps / 10 for the tolerance that selects w (floor 1e-14); and against the oracle's own fit
+    (complex-square Vandermonde, a different method) to within the sum of their bounds."""
+    z = np.linspace(-1, 1, 3001)
+    for w in range(2, 17):
+        beta = oracle_mod.es_beta(w, sigma)
+        st, C = lib.nufft_horner_coeffs(w, beta)
+        assert st == 0
+        C = np.asarray(C)
+        assert C.shape == (w, w + 4)
+        mine = oracle_mod.piecewise_eval(C, w, z)
+        err = np.abs(mine - oracle_mod.es_kernel(z, beta)).max()
+        eps_w = _eps_of_width(oracle_mod, w, sigma)
+        assert err <= max(0.1 * eps_w, 1e-14), (w, err)
+        theirs = oracle_mod.piecewise_eval(oracle_mod.piecewise_poly(w, beta), w, z)
+        assert np.abs(mine - theirs).max() <= max(0.6 * eps_w, 2e-14)
+
+
+def test_horner_coeffs_rejects_bad_args(lib):
+    assert lib.nufft_horner_coeffs(1, 5.0)[0] == -1
+    assert lib.nufft_horner_coeffs(17, 5.0)[0] == -1
+    assert lib.nufft_horner_coeffs(6, 0.0)[0] == -1

@@ -335,3 +335,46 @@ def test_parity_sigma54(pkg, oracle_mod, cdtype, eps, d):
     tol = TOL_SAME[cdtype] * rmax(w, beta, 1.25) / rmax(w2, b2, 2.0)
     assert oracle_mod.rel_l2(g1[0], o2_1) <= tol
     assert oracle_mod.rel_l2(g2[0], o2_2) <= tol
+
+
+# Sec. 5.3's piecewise polynomial kernel (opts.kerevalmeth = 1): the transform stays within
+# 10 eps of the exact sums; against the same plan with the ES formula the two differ by the
+# polynomial's approximation error (below eps / 10 per kernel value, host-tested), so their
+# relative difference stays below eps.  Dense (tiled) and sparse (per-warp) subproblems both
+# run: the uniform case fills the bins, the low-density case (M small) leaves most of them
+# with a handful of points.
+HORNER_CASES = [(np.complex64, 1e-3), (np.complex64, 1e-5), (np.complex128, 1e-9), (np.complex128, 1e-12)]
+
+
+@pytest.mark.parametrize("cdtype,eps", HORNER_CASES)
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("dense", [True, False])
+def test_parity_horner_kernel(pkg, oracle_mod, cdtype, eps, d, dense):
+    Ns, M = SIZES[d]
+    if not dense:
+        M = M // 20
+    xs, c, f = case_inputs(d, Ns, M, "uniform", cdtype, seed=4000 + 10 * d + dense)
+    x64 = [v.astype(np.float64) for v in xs]
+    h1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, kerevalmeth=1)
+    h2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, kerevalmeth=1)
+    e1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype)
+    e2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype)
+    assert oracle_mod.rel_l2(h1[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= 10 * eps
+    assert oracle_mod.rel_l2(h2[0], oracle_mod.direct_type2(x64, f, -1, Ns)) <= 10 * eps
+    floor = TOL_SAME[cdtype]
+    assert oracle_mod.rel_l2(h1[0], e1[0]) <= max(eps, floor)
+    assert oracle_mod.rel_l2(h2[0], e2[0]) <= max(eps, floor)
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex128, 1e-11)])
+def test_horner_edge_points(pkg, oracle_mod, cdtype, eps):
+    """Points on grid nodes (f = 0: the node at the support's end), half cells, bin edges."""
+    d = 3
+    Ns = [16, 12, 10]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    xs, M = I.edge_points(d, ns, dtype=rdt)
+    c = I.complex_normal(7, M, dtype=cdtype)
+    x64 = [v.astype(np.float64) for v in xs]
+    g1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, kerevalmeth=1)
+    assert oracle_mod.rel_l2(g1[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= 10 * eps
