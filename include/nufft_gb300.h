@@ -73,8 +73,9 @@ typedef struct {
                          on the fine grid instead of through a shared-memory tile (0: 32, -1: never) */
   int kerevalmeth;    /* kernel evaluation in the spread / interp kernels: 0 the ES formula (one exp and one
                          sqrt per node), 1 the piecewise polynomial of Sec. 5.3 (w intervals of degree
-                         w + 3, Horner's scheme; see nufft_horner_coeffs).  The complex128 interpolation
-                         (double-float) and the gradient kernels always use the formula. */
+                         w + 3, Horner's scheme; see nufft_horner_coeffs; the autotuner tries both).
+                         The complex128 interpolation (double-float) and the gradient kernels always
+                         use the formula. */
   int reserved[6];    /* set to zero */
   double upsampfac;   /* fine grid / modes per dimension, sigma: 2 (0 means 2) or 1.25 (smaller FFTs and
                          grids, wider kernel: w from the slope of Eq. (ESerr), beta from Eq. (gam); more

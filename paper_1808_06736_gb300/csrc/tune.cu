@@ -128,9 +128,9 @@ int search(int dim, bool dbl, int w, bool try_sigma54, Trial& t, cudaStream_t st
     o.threads = 128;
     consider(o);
   }
-  {  // Sec. 5.3's piecewise polynomial instead of exp and sqrt per kernel value
+  {  // the other kernel evaluation (Sec. 5.3's piecewise polynomial, or exp and sqrt per value)
     nufft_opts o = cur;
-    o.kerevalmeth = 1;
+    o.kerevalmeth = 1 - cur.kerevalmeth;
     consider(o);
   }
   if (try_sigma54) {  // smaller grids and FFTs for a wider kernel; its own default bins

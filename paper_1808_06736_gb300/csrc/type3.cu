@@ -37,6 +37,7 @@ constexpr int kMaxGL = 32;  // p = ceil(1.5 w + 2) <= 26 for w <= 16
 struct GLRule {
   double q[kMaxGL];   // positive nodes
   double wf[kMaxGL];  // weight * phi(node)
+  float qf[kMaxGL], wff[kMaxGL];  // the same, rounded to float
   int p;
 };
 
@@ -44,6 +45,43 @@ template <typename T>
 struct CT {
   T x, y;
 };
+
+// e^{i a} for a phase formed in double.  complex64: a reduced to [-pi, pi]
+// in double, then the float sine and cosine (error ~1e-7, below what float
+// coordinates already carry); complex128: the double ones.
+template <typename T>
+__device__ __forceinline__ CT<T> unit_phase(double a);
+template <>
+__device__ __forceinline__ CT<float> unit_phase<float>(double a) {
+  const double r = a - 6.283185307179586 * rint(a * 0.15915494309189535);
+  float sn, cs;
+  sincosf((float)r, &sn, &cs);
+  return CT<float>{cs, sn};
+}
+template <>
+__device__ __forceinline__ CT<double> unit_phase<double>(double a) {
+  double sn, cs;
+  sincos(a, &sn, &cs);
+  return CT<double>{cs, sn};
+}
+
+// phi^(xi) / 2 = sum_q w_q phi(q) cos(xi q) over the positive Gauss-Legendre
+// nodes (Eq. (quad)); complex64 plans sum in float (|xi q| < 2 pi w)
+template <typename T>
+__device__ __forceinline__ double half_ft(double xi, const GLRule& gl);
+template <>
+__device__ __forceinline__ double half_ft<float>(double xi, const GLRule& gl) {
+  const float xf = (float)xi;
+  float ft = 0.0f;
+  for (int q = 0; q < gl.p; ++q) ft = fmaf(gl.wff[q], cosf(xf * gl.qf[q]), ft);
+  return (double)ft;
+}
+template <>
+__device__ __forceinline__ double half_ft<double>(double xi, const GLRule& gl) {
+  double ft = 0.0;
+  for (int q = 0; q < gl.p; ++q) ft += gl.wf[q] * cos(xi * gl.q[q]);
+  return ft;
+}
 
 // per-dimension min and max of up to three coordinate arrays, one partial per block
 template <typename T>
@@ -101,9 +139,7 @@ __global__ void k_t3_sources(int64_t M, int d, const T* __restrict__ x, const T*
     xo[j] = (T)(u0 * src.scale[0]);
     if (d > 1) yo[j] = (T)(u1 * src.scale[1]);
     if (d > 2) zo[j] = (T)(u2 * src.scale[2]);
-    double sn, cs;
-    sincos((double)isign * (s0x * u0 + s0y * u1 + s0z * u2), &sn, &cs);
-    phase[j] = CT<T>{(T)cs, (T)sn};
+    phase[j] = unit_phase<T>((double)isign * (s0x * u0 + s0y * u1 + s0z * u2));
   }
 }
 
@@ -124,13 +160,10 @@ __global__ void k_t3_targets(int64_t N, int d, const T* __restrict__ s, const T*
       if (i == 1) to[k] = (T)so_i;
       if (i == 2) uo[k] = (T)so_i;
       const double xi = alpha_gamma[i] * sc;  // alpha_i s'_i with s' = gamma (s - s0)
-      double ft = 0.0;
-      for (int q = 0; q < gl.p; ++q) ft += gl.wf[q] * cos(xi * gl.q[q]);
-      p *= 2.0 / (w * 2.0 * ft);
+      p *= 2.0 / (w * 2.0 * half_ft<T>(xi, gl));
     }
-    double sn, cs;
-    sincos((double)isign * (v[0] * x0x + v[1] * x0y + v[2] * x0z), &sn, &cs);
-    corr[k] = CT<T>{(T)(p * cs), (T)(p * sn)};
+    const CT<T> e = unit_phase<T>((double)isign * (v[0] * x0x + v[1] * x0y + v[2] * x0z));
+    corr[k] = CT<T>{(T)p * e.x, (T)p * e.y};
   }
 }
 
@@ -348,6 +381,8 @@ int setpts_t(nufft_plan3 p, int64_t M, const void* x, const void* y, const void*
     for (int j = 0; j < gl.p; ++j) {
       gl.q[j] = q[(size_t)j];
       gl.wf[j] = wq[(size_t)j] * std::exp(p->beta * (std::sqrt(1.0 - q[(size_t)j] * q[(size_t)j]) - 1.0));
+      gl.qf[j] = (float)gl.q[j];
+      gl.wff[j] = (float)gl.wf[j];
     }
     k_t3_targets<T><<<blocks_for(N), 256, 0, p->stream>>>(
         N, d, (const T*)s, (const T*)(t ? t : s), (const T*)(u ? u : s), tgt, p->x0[0], p->x0[1], p->x0[2], p->isign,
