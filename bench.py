@@ -40,16 +40,16 @@ METRIC = "type1/2 NU points/s at eps=1e-5 (3D, fp32)"
 # valid only for the kernel source they were measured on.
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1808_06736_gb300", "csrc", "spread_interp.cuh")
 MEASURED_TRAFFIC = {
-    "sha256": "4e42bd3250a97faacc77fa0758c17ec398bba237e10c0d16591c80ae26ab243c",
-    "spread": 15070201600 + 1226339072,
-    "interp": 6020471040 + 3177263104,
+    "sha256": "d2464df117258f916c17f3d21cf031426fe7e19d2e0a57d31cd25cebed4ebc0c",
+    "spread": 15070313984 + 1226657280,
+    "interp": 6020101120 + 3177227776,
 }
 
 
 def measured_traffic(kernel: str, args) -> int | None:
     import hashlib
     default = (args.M == 100_000_000 and args.N == 256 and args.eps == 1e-5 and args.kind == "uniform" and
-               args.prec == "c64")
+               args.prec == "c64" and args.kerevalmeth == 0)
     try:
         digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
     except OSError:

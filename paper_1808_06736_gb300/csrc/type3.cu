@@ -65,38 +65,40 @@ __device__ __forceinline__ CT<double> unit_phase<double>(double a) {
   return CT<double>{cs, sn};
 }
 
-// phi^(xi) / 2 = sum_q w_q phi(q) cos(xi q) over the positive Gauss-Legendre
-// nodes (Eq. (quad)); complex64 plans sum in float (|xi q| < 2 pi w)
+// 2 / (w phi^(xi)) with phi^(xi) = 2 sum_q w_q phi(q) cos(xi q) over the
+// positive Gauss-Legendre nodes (Eq. (quad)); complex64 plans work in float
+// (|xi q| < 2 pi w; the FP64 pipe would otherwise bind this kernel)
 template <typename T>
-__device__ __forceinline__ double half_ft(double xi, const GLRule& gl);
+__device__ __forceinline__ T corr_factor(double xi, T w, const GLRule& gl);
 template <>
-__device__ __forceinline__ double half_ft<float>(double xi, const GLRule& gl) {
+__device__ __forceinline__ float corr_factor<float>(double xi, float w, const GLRule& gl) {
   const float xf = (float)xi;
   float ft = 0.0f;
   for (int q = 0; q < gl.p; ++q) ft = fmaf(gl.wff[q], cosf(xf * gl.qf[q]), ft);
-  return (double)ft;
+  return 1.0f / (w * ft);
 }
 template <>
-__device__ __forceinline__ double half_ft<double>(double xi, const GLRule& gl) {
+__device__ __forceinline__ double corr_factor<double>(double xi, double w, const GLRule& gl) {
   double ft = 0.0;
   for (int q = 0; q < gl.p; ++q) ft += gl.wf[q] * cos(xi * gl.q[q]);
-  return ft;
+  return 1.0 / (w * ft);
 }
 
 // per-dimension min and max of up to three coordinate arrays, one partial per block
 template <typename T>
 __global__ void k_minmax(int64_t n, int d, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c,
                          double* __restrict__ part) {
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  // min and max are exact in the input precision; partials are widened at the end
+  T mn[3] = {T(INFINITY), T(INFINITY), T(INFINITY)}, mx[3] = {-T(INFINITY), -T(INFINITY), -T(INFINITY)};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T v[3] = {a[i], d > 1 ? b[i] : T(0), d > 2 ? c[i] : T(0)};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      mn[k] = fmin(mn[k], (double)v[k]);
-      mx[k] = fmax(mx[k], (double)v[k]);
+      mn[k] = fmin(mn[k], v[k]);
+      mx[k] = fmax(mx[k], v[k]);
     }
   }
-  __shared__ double smn[3][32], smx[3][32];
+  __shared__ T smn[3][32], smx[3][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -112,13 +114,13 @@ __global__ void k_minmax(int64_t n, int d, const T* __restrict__ a, const T* __r
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < 3; ++k) {
-      double u = INFINITY, v = -INFINITY;
+      T u = T(INFINITY), v = -T(INFINITY);
       for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
         u = fmin(u, smn[k][q]);
         v = fmax(v, smx[k][q]);
       }
-      part[blockIdx.x * 6 + k] = u;
-      part[blockIdx.x * 6 + 3 + k] = v;
+      part[blockIdx.x * 6 + k] = (double)u;
+      part[blockIdx.x * 6 + 3 + k] = (double)v;
     }
   }
 }
@@ -152,18 +154,18 @@ __global__ void k_t3_targets(int64_t N, int d, const T* __restrict__ s, const T*
                              T* __restrict__ to, T* __restrict__ uo, CT<T>* __restrict__ corr) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
     const double v[3] = {(double)s[k], d > 1 ? (double)t[k] : 0.0, d > 2 ? (double)u[k] : 0.0};
-    double p = 1.0;
+    T p = T(1);
     for (int i = 0; i < d; ++i) {
       const double sc = v[i] - tgt.shift[i];
       const double so_i = sc * tgt.scale[i];
       if (i == 0) so[k] = (T)so_i;
       if (i == 1) to[k] = (T)so_i;
       if (i == 2) uo[k] = (T)so_i;
-      const double xi = alpha_gamma[i] * sc;  // alpha_i s'_i with s' = gamma (s - s0)
-      p *= 2.0 / (w * 2.0 * half_ft<T>(xi, gl));
+      // alpha_i s'_i with s' = gamma (s - s0)
+      p *= corr_factor<T>(alpha_gamma[i] * sc, (T)w, gl);
     }
     const CT<T> e = unit_phase<T>((double)isign * (v[0] * x0x + v[1] * x0y + v[2] * x0z));
-    corr[k] = CT<T>{(T)p * e.x, (T)p * e.y};
+    corr[k] = CT<T>{p * e.x, p * e.y};
   }
 }
 
