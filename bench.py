@@ -60,6 +60,7 @@ def measured_traffic(kernel: str, args) -> int | None:
 UNIT = "NU points/s"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
+SMEM_ATOMIC_PEAK = 5.73e12  # 32-bit shared-memory atomic adds per second, lane-consecutive addresses (measured)
 
 
 def parse():
@@ -336,6 +337,14 @@ def run_cuda(args, ws, rank, local):
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": measured_traffic(dominant, args), "peak_source": src,
             "algorithmic_flops_per_point": algorithmic_units(d, w)}
+    if dominant == "spread" and args.prec == "c64":
+        # the unit that binds the complex64 spread: shared-memory integer atomics, two per
+        # stencil cell (real and imaginary fixed-point parts)
+        atoms = 2 * w ** d * M
+        roof["smem_atomics"] = {
+            "achieved_per_s": atoms / (med["spread"] * 1e-3), "peak_per_s": SMEM_ATOMIC_PEAK,
+            "frac": atoms / (med["spread"] * 1e-3) / SMEM_ATOMIC_PEAK, "atomics_per_launch": atoms,
+            "peak_source": "measured: conflict-free 32-bit shared-memory atomic adds, 152x4 blocks of 256 threads"}
     kernels_ms = {k: round(v, 4) for k, v in med.items()}
     p1.close()
     p2.close()

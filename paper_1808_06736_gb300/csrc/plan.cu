@@ -840,12 +840,19 @@ int nufft_get_timings(nufft_plan p, double* ms, int n) {
   if (!p->ev_ok) return 0;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
   int k = 0;
+  bool missing = false;
   for (int i = 0; i < 6 && k < n; ++i, ++k) {
     float v = 0.f;
     int a = i < 3 ? i : i + 1;  // slots 0-3 setpts, 4-7 execute
-    if (cudaEventElapsedTime(&v, p->ev[a], p->ev[a + 1]) != cudaSuccess) v = -1.f;
+    if (cudaEventElapsedTime(&v, p->ev[a], p->ev[a + 1]) != cudaSuccess) {
+      v = -1.f;  // a step not run since the plan was made
+      missing = true;
+    }
     ms[k] = v;
   }
+  // an event never recorded fails cudaEventElapsedTime with a non-sticky error that would
+  // otherwise be reported by the next launch check of this thread
+  if (missing) cudaGetLastError();
   return k;
 }
 

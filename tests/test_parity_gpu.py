@@ -383,3 +383,21 @@ def test_horner_edge_points(pkg, oracle_mod, cdtype, eps):
     x64 = [v.astype(np.float64) for v in xs]
     g1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, kerevalmeth=1)
     assert oracle_mod.rel_l2(g1[0], oracle_mod.direct_type1(x64, c, 1, Ns)) <= 10 * eps
+
+
+def test_timings_before_execute_leave_no_error(pkg):
+    """nufft_get_timings right after setpts (the execute events not recorded yet) reports -1
+    for those steps and leaves no CUDA error behind: the next setpts and execute succeed."""
+    import torch
+    dev = torch.device("cuda:0")
+    p = pkg.Plan(1, [32, 24, 16], eps=1e-5, dtype=torch.complex64, device=dev, debug=1)
+    xs = [torch.from_numpy(v).to(dev) for v in I.points(11, 5000, 3, dtype=np.float32)]
+    p.setpts(*xs)
+    t = p.timings()
+    assert all(v >= 0 for v in t[:3]) and all(v == -1 for v in t[3:])
+    p.setpts(*xs)
+    p.execute(torch.ones(5000, dtype=torch.complex64, device=dev))
+    t = p.timings()
+    assert all(v >= 0 for v in t)
+    assert p.status() == 0
+    p.close()
