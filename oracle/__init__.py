@@ -73,8 +73,10 @@ def _L():
         lib.oracle_type1_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ctypes.c_int, i64, ip, dp]
         lib.oracle_type2_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, ip, dp, ctypes.c_int, dp]
         lib.oracle_type3_direct.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ctypes.c_int, i64, dp, dp, dp, dp]
-        lib.oracle_spread.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double, dp]
-        lib.oracle_interp.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double, dp]
+        lib.oracle_spread.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int, dp]
+        lib.oracle_interp.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -233,6 +235,28 @@ def choose_params(eps: float, Ns, sigma: float = 2.0):
 
 
 # --------------------------------------------------- kernel and its transform
+KERNELS = {"es": 0, "cosh": 1}
+
+
+def es_cosh_kernel(z, beta: float):
+    """The smooth variant of the Remark in Sec. 7: 2 exp(-beta) cosh(beta sqrt(1 - z^2)) on
+    |z| <= 1, zero outside (within exp(-beta) of Eq. (ES), with bounded derivatives)."""
+    z = np.asarray(z, dtype=np.float64)
+    out = np.zeros_like(z)
+    m = np.abs(z) <= 1.0
+    out[m] = 2.0 * np.exp(-beta) * np.cosh(beta * np.sqrt(1.0 - z[m] ** 2))
+    return out
+
+
+def kernel_fn(kernel: str, beta: float):
+    """phi as a function of z for kernel 'es' (Eq. (ES)) or 'cosh' (Remark in Sec. 7)."""
+    if kernel == "es":
+        return lambda z: es_kernel(z, beta)
+    if kernel == "cosh":
+        return lambda z: es_cosh_kernel(z, beta)
+    raise ValueError(kernel)
+
+
 def es_kernel(z, beta: float):
     """Eq. (ES): exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, zero outside."""
     z = np.asarray(z, dtype=np.float64)
@@ -301,26 +325,26 @@ def kernel_ft(xi, w: int, beta: float, kernel=None):
     return 2.0 * (np.cos(np.outer(xi, q)) @ (wq * phi))
 
 
-def correction_factors(N: int, n: int, w: int, beta: float) -> np.ndarray:
+def correction_factors(N: int, n: int, w: int, beta: float, kernel: str = "es") -> np.ndarray:
     """Eq. (pk1): p_k = h / psi^(k) = 2 / (w phi^(alpha k)), alpha = pi w / n (Eq. (al)), k in I_N."""
     alpha = math.pi * w / n
-    return 2.0 / (w * kernel_ft(alpha * mode_range(N), w, beta))
+    return 2.0 / (w * kernel_ft(alpha * mode_range(N), w, beta, kernel=kernel_fn(kernel, beta)))
 
 
 # ------------------------------------------------------------- O2 pieces
-def spread(xs, c, ns, w: int, beta: float) -> np.ndarray:
+def spread(xs, c, ns, w: int, beta: float, kernel: str = "es") -> np.ndarray:
     """Eq. (bl): fine-grid values b_l (complex, shape (n_d, ..., n_1))."""
     d, xs, full = _coords(xs)
     c = _cplx(c)
     n = np.ascontiguousarray(ns, dtype=np.int64)
     b = np.zeros(int(np.prod(n)), dtype=np.complex128)
     _L().oracle_spread(d, c.shape[0], _dptr(full[0]), _dptr(full[1]), _dptr(full[2]),
-                       _dptr(c.view(np.float64)), _iptr(n), int(w), float(beta),
+                       _dptr(c.view(np.float64)), _iptr(n), int(w), float(beta), KERNELS[kernel],
                        _dptr(b.view(np.float64)))
     return b.reshape(tuple(reversed([int(v) for v in ns])))
 
 
-def interp(xs, b, ns, w: int, beta: float) -> np.ndarray:
+def interp(xs, b, ns, w: int, beta: float, kernel: str = "es") -> np.ndarray:
     """Eq. (interp): c_j = sum_l b_l psi~(l h - x_j)."""
     d, xs, full = _coords(xs)
     b = _cplx(b).ravel()
@@ -328,7 +352,7 @@ def interp(xs, b, ns, w: int, beta: float) -> np.ndarray:
     M = xs[0].shape[0]
     c = np.zeros(M, dtype=np.complex128)
     _L().oracle_interp(d, M, _dptr(full[0]), _dptr(full[1]), _dptr(full[2]),
-                       _dptr(b.view(np.float64)), _iptr(n), int(w), float(beta),
+                       _dptr(b.view(np.float64)), _iptr(n), int(w), float(beta), KERNELS[kernel],
                        _dptr(c.view(np.float64)))
     return c
 
@@ -350,48 +374,49 @@ def _truncation_index(Ns, ns):
     return np.ix_(*[np.mod(mode_range(N), n) for N, n in zip(reversed(Ns), reversed(ns))])
 
 
-def _outer_correction(Ns, ns, w, beta):
+def _outer_correction(Ns, ns, w, beta, kernel="es"):
     """Eq. (pk): the separable p_k as an array of shape (N_d, ..., N_1)."""
     p = None
     for N, n in zip(reversed(Ns), reversed(ns)):
-        pk = correction_factors(N, n, w, beta)
+        pk = correction_factors(N, n, w, beta, kernel)
         p = pk if p is None else np.multiply.outer(p, pk)
     return p
 
 
-def deconvolve(bh: np.ndarray, Ns, ns, w: int, beta: float) -> np.ndarray:
+def deconvolve(bh: np.ndarray, Ns, ns, w: int, beta: float, kernel: str = "es") -> np.ndarray:
     """Type-1 step 3, Eq. (pb1) with Eq. (pk): f_k = p_k b^_{k mod n} for k in I_N (mode order)."""
-    return (bh[_truncation_index(Ns, ns)] * _outer_correction(Ns, ns, w, beta)).ravel()
+    return (bh[_truncation_index(Ns, ns)] * _outer_correction(Ns, ns, w, beta, kernel)).ravel()
 
 
-def precorrect(f, Ns, ns, w: int, beta: float) -> np.ndarray:
+def precorrect(f, Ns, ns, w: int, beta: float, kernel: str = "es") -> np.ndarray:
     """Type-2 step 1 (Sec. 3.2): b^_{k mod n} = p_k f_k on I_N, zero elsewhere on the fine grid."""
     f = _cplx(f).reshape(tuple(reversed([int(v) for v in Ns])))
     bh = np.zeros(tuple(reversed([int(v) for v in ns])), dtype=np.complex128)
-    bh[_truncation_index(Ns, ns)] = f * _outer_correction(Ns, ns, w, beta)
+    bh[_truncation_index(Ns, ns)] = f * _outer_correction(Ns, ns, w, beta, kernel)
     return bh
 
 
 def type1(xs, c, isign: int, Ns, eps: float | None = None, w: int | None = None,
-          beta: float | None = None, ns=None) -> np.ndarray:
+          beta: float | None = None, ns=None, kernel: str = "es") -> np.ndarray:
     """O2 type 1 (Sec. 3.1): spread Eq. (bl), DFT Eq. (dft1) with sign isign, truncate and
-    correct Eq. (pb1)/(pk).  Parameters from eps unless (w, beta, ns) are given."""
+    correct Eq. (pb1)/(pk).  Parameters from eps unless (w, beta, ns) are given; kernel 'es'
+    (Eq. (ES)) or 'cosh' (Remark in Sec. 7, same w and beta)."""
     Ns = [int(v) for v in Ns]
     if w is None:
         w, beta, ns = choose_params(eps, Ns)
-    b = spread(xs, c, ns, w, beta)
-    return deconvolve(dft(b, isign), Ns, ns, w, beta)
+    b = spread(xs, c, ns, w, beta, kernel)
+    return deconvolve(dft(b, isign), Ns, ns, w, beta, kernel)
 
 
 def type2(xs, f, isign: int, Ns, eps: float | None = None, w: int | None = None,
-          beta: float | None = None, ns=None) -> np.ndarray:
+          beta: float | None = None, ns=None, kernel: str = "es") -> np.ndarray:
     """O2 type 2 (Sec. 3.2): pre-correct and zero-pad, DFT Eq. (dft) with sign isign,
     interpolate Eq. (interp)."""
     Ns = [int(v) for v in Ns]
     if w is None:
         w, beta, ns = choose_params(eps, Ns)
-    b = dft(precorrect(f, Ns, ns, w, beta), isign)
-    return interp(xs, b, ns, w, beta)
+    b = dft(precorrect(f, Ns, ns, w, beta, kernel), isign)
+    return interp(xs, b, ns, w, beta, kernel)
 
 
 # ------------------------------------------------------------- O2 type 3

@@ -164,9 +164,16 @@ void oracle_type2_direct(int d, int64_t nt, const double* xt, const double* yt, 
   free(part);
 }
 
-/* ES kernel, Eq. (ES): phi(z) = exp(beta (sqrt(1 - z^2) - 1)) for |z| <= 1, else 0. */
-static double es_kernel(double z, double beta) {
+/*
+ * kernel = 0: the ES kernel, Eq. (ES): phi(z) = exp(beta (sqrt(1 - z^2) - 1)).
+ * kernel = 1: its smooth variant of the Remark in Sec. 7,
+ *   phi(z) = 2 exp(-beta) cosh(beta sqrt(1 - z^2)),
+ * a power series in 1 - z^2, so smooth up to z = +-1, and within exp(-beta) of ES.
+ * Both are zero for |z| > 1.
+ */
+static double es_kernel(double z, double beta, int kernel) {
   if (fabs(z) > 1.0) return 0.0;
+  if (kernel == 1) return 2.0 * exp(-beta) * cosh(beta * sqrt(1.0 - z * z));
   return exp(beta * (sqrt(1.0 - z * z) - 1.0));
 }
 
@@ -181,13 +188,13 @@ static double es_kernel(double z, double beta) {
  * weight exp(-beta)).  Each node is reported by its index modulo n, which is
  * how the periodisation acts on the grid since n >= 2w.
  */
-static void node_weights(double x, int64_t n, int w, double beta, int64_t* idx, double* ker) {
+static void node_weights(double x, int64_t n, int w, double beta, int kernel, int64_t* idx, double* ker) {
   const double two_pi = 6.283185307179586476925286766559;
   double u = x * (double)n / two_pi;
   double l0 = ceil(u - 0.5 * (double)w);
   for (int t = 0; t < w; ++t) {
     double l = l0 + (double)t;
-    ker[t] = es_kernel((l - u) * 2.0 / (double)w, beta);
+    ker[t] = es_kernel((l - u) * 2.0 / (double)w, beta, kernel);
     int64_t li = (int64_t)l % n;
     if (li < 0) li += n;
     idx[t] = li;
@@ -202,7 +209,7 @@ static void node_weights(double x, int64_t n, int w, double beta, int64_t* idx, 
  * the w^d nodes of each point.
  */
 void oracle_spread(int d, int64_t M, const double* x, const double* y, const double* z,
-                   const double* c, const int64_t* n, int w, double beta, double* b) {
+                   const double* c, const int64_t* n, int w, double beta, int kernel, double* b) {
   int64_t nn[3] = {1, 1, 1}, nt = 1;
   for (int i = 0; i < d; ++i) { nn[i] = n[i]; nt *= n[i]; }
   memset(b, 0, sizeof(double) * 2 * (size_t)nt);
@@ -211,7 +218,7 @@ void oracle_spread(int d, int64_t M, const double* x, const double* y, const dou
   for (int64_t j = 0; j < M; ++j) {
     int w2 = d >= 2 ? w : 1, w3 = d >= 3 ? w : 1;
     for (int i = 0; i < 3; ++i) {
-      if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, idx[i], ker[i]);
+      if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, kernel, idx[i], ker[i]);
       else { idx[i][0] = 0; ker[i][0] = 1.0; }
     }
     for (int t3 = 0; t3 < w3; ++t3)
@@ -232,7 +239,7 @@ void oracle_spread(int d, int64_t M, const double* x, const double* y, const dou
  * transpose of that spreading map.
  */
 void oracle_interp(int d, int64_t M, const double* x, const double* y, const double* z,
-                   const double* b, const int64_t* n, int w, double beta, double* c) {
+                   const double* b, const int64_t* n, int w, double beta, int kernel, double* c) {
   int64_t nn[3] = {1, 1, 1};
   for (int i = 0; i < d; ++i) nn[i] = n[i];
   int64_t idx[3][32];
@@ -240,7 +247,7 @@ void oracle_interp(int d, int64_t M, const double* x, const double* y, const dou
   for (int64_t j = 0; j < M; ++j) {
     int w2 = d >= 2 ? w : 1, w3 = d >= 3 ? w : 1;
     for (int i = 0; i < 3; ++i) {
-      if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, idx[i], ker[i]);
+      if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, kernel, idx[i], ker[i]);
       else { idx[i][0] = 0; ker[i][0] = 1.0; }
     }
     double sr = 0, si = 0;

@@ -296,7 +296,7 @@ def test_planted_mistakes_are_caught(oracle_mod, monkeypatch):
     assert base < 1e-5
     # (a) a dropped factor 2/w in Eq. (pk1)
     orig_cf = oracle_mod.correction_factors
-    monkeypatch.setattr(oracle_mod, "correction_factors", lambda N, n, w, b: orig_cf(N, n, w, b) * w / 2)
+    monkeypatch.setattr(oracle_mod, "correction_factors", lambda N, n, w, b, k="es": orig_cf(N, n, w, b, k) * w / 2)
     assert _err_t1(oracle_mod) > 1e-1
     monkeypatch.setattr(oracle_mod, "correction_factors", orig_cf)
     # (b) the wrong DFT sign
@@ -312,14 +312,14 @@ def test_planted_mistakes_are_caught(oracle_mod, monkeypatch):
     # (d) each dimension's correction computed with another dimension's fine-grid size
     orig_outer = oracle_mod._outer_correction
     monkeypatch.setattr(oracle_mod, "_outer_correction",
-                        lambda Ns, ns, w, b: orig_outer(Ns, list(ns)[::-1], w, b))
+                        lambda Ns, ns, w, b, k="es": orig_outer(Ns, list(ns)[::-1], w, b, k))
     assert _err_t1(oracle_mod) > 1e-3
     monkeypatch.setattr(oracle_mod, "_outer_correction", orig_outer)
     # (e) the nodes of a coordinate starting one cell late (ceil(u - w/2) + 1)
     orig_spread = oracle_mod.spread
     monkeypatch.setattr(oracle_mod, "spread",
-                        lambda xs, c, ns, w, b: orig_spread([np.asarray(v) - 2 * math.pi / n for v, n in zip(xs, ns)],
-                                                            c, ns, w, b))
+                        lambda xs, c, ns, w, b, k="es": orig_spread(
+                            [np.asarray(v) - 2 * math.pi / n for v, n in zip(xs, ns)], c, ns, w, b, k))
     assert _err_t1(oracle_mod) > 1e-1
     monkeypatch.setattr(oracle_mod, "spread", orig_spread)
     assert _err_t1(oracle_mod) == pytest.approx(base)
@@ -492,3 +492,52 @@ def test_piecewise_poly_planted_mistakes(oracle_mod):
     rolled = np.roll(C, 1, axis=0)                         # interval t uses t - 1's polynomial
     for bad in (flipped, rolled):
         assert np.abs(oracle_mod.piecewise_eval(bad, w, z) - ref).max() > 100 * bound
+
+
+# ------------------------------------------------ smooth (cosh) kernel variant
+def test_cosh_kernel_closed_forms(oracle_mod):
+    """Remark in Sec. 7: 2 e^-beta cosh(beta sqrt(1 - z^2)) = ES + e^{-beta (sqrt(1 - z^2) + 1)},
+    so it lies within e^-beta of ES (the gap is largest at z = +-1), equals 1 + e^{-2 beta} at 0,
+    and its derivative tends to the finite -2 beta^2 e^-beta z at the support's ends, where
+    ES's derivative is unbounded."""
+    beta = oracle_mod.es_beta(7)
+    z = np.linspace(-1, 1, 2001)
+    gap = oracle_mod.es_cosh_kernel(z, beta) - oracle_mod.es_kernel(z, beta)
+    np.testing.assert_allclose(gap, np.exp(-beta * (np.sqrt(1 - z * z) + 1)), rtol=1e-9, atol=4e-15)  # the difference of two O(1) values
+    assert gap.max() <= math.exp(-beta) * (1 + 1e-12)
+    assert oracle_mod.es_cosh_kernel(np.array([0.0]), beta)[0] == pytest.approx(1 + math.exp(-2 * beta), rel=1e-15)
+    h = 1e-7
+    for z0 in (1 - 1e-6, 1 - 1e-9):
+        fd = (oracle_mod.es_cosh_kernel(np.array([z0]), beta)[0]
+              - oracle_mod.es_cosh_kernel(np.array([z0 - h]), beta)[0]) / h
+        assert fd == pytest.approx(-2 * beta ** 2 * math.exp(-beta), rel=1e-3)
+        fd_es = (oracle_mod.es_kernel(np.array([z0]), beta)[0]
+                 - oracle_mod.es_kernel(np.array([z0 - h]), beta)[0]) / h
+        assert abs(fd_es) > 10 * abs(fd)
+
+
+@pytest.mark.parametrize("w", [2, 4, 6, 10, 16])
+def test_cosh_kernel_ft_vs_adaptive_quadrature(oracle_mod, w):
+    """The Gauss-Legendre rule of Eq. (quad) on the cosh kernel against scipy's adaptive quadrature."""
+    beta = oracle_mod.es_beta(w)
+    xi = np.linspace(0.0, math.pi * w / 4.0, 7)
+    gl = oracle_mod.kernel_ft(xi, w, beta, kernel=oracle_mod.kernel_fn("cosh", beta))
+    f = lambda z, x: 2 * math.exp(-beta) * math.cosh(beta * math.sqrt(max(1 - z * z, 0.0))) * math.cos(x * z)  # noqa: E731
+    ref = np.array([2.0 * integrate.quad(f, 0.0, 1.0, args=(v,), epsabs=0.0, epsrel=1e-12, limit=800)[0]
+                    for v in xi])
+    assert np.max(np.abs(gl - ref) / np.abs(ref)) < max(10.0 ** (-(w - 1)), 1e-14)
+
+
+@pytest.mark.parametrize("d,Ns,M", CASES)
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-10])
+def test_o2_cosh_error_vs_truth(oracle_mod, d, Ns, M, eps):
+    """O2 with the cosh kernel (same w, beta) against the exact sums: within 10 eps, and within
+    a few eps of O2 with ES (the kernels differ by at most e^-beta)."""
+    xs = I.points(11, M, d)
+    c = I.complex_normal(12, M)
+    f = I.complex_normal(13, int(np.prod(Ns)))
+    t1 = oracle_mod.type1(xs, c, 1, Ns, eps=eps, kernel="cosh")
+    t2 = oracle_mod.type2(xs, f, -1, Ns, eps=eps, kernel="cosh")
+    assert oracle_mod.rel_l2(t1, oracle_mod.direct_type1(xs, c, 1, Ns)) <= 10 * eps
+    assert oracle_mod.rel_l2(t2, oracle_mod.direct_type2(xs, f, -1, Ns)) <= 10 * eps
+    assert oracle_mod.rel_l2(t1, oracle_mod.type1(xs, c, 1, Ns, eps=eps)) <= 3 * eps
