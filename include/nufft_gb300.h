@@ -76,7 +76,10 @@ typedef struct {
                          w + 3, Horner's scheme; see nufft_horner_coeffs; the autotuner tries both).
                          The complex128 interpolation (double-float) and the gradient kernels always
                          use the formula. */
-  int reserved[6];    /* set to zero */
+  int kernel;         /* 0: the ES kernel, Eq. (ES); 1: its smooth variant 2 e^-beta cosh(beta sqrt(1 - z^2))
+                         (Remark in Sec. 7: within e^-beta of ES, bounded derivatives; same w and beta, its
+                         own correction factors), for point gradients (nufft_execute_grad) */
+  int reserved[5];    /* set to zero */
   double upsampfac;   /* fine grid / modes per dimension, sigma: 2 (0 means 2) or 1.25 (smaller FFTs and
                          grids, wider kernel: w from the slope of Eq. (ESerr), beta from Eq. (gam); more
                          rounding amplification, see nufft_choose_params_sigma) */

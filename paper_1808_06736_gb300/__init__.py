@@ -45,7 +45,8 @@ class NufftError(RuntimeError):
 class nufft_opts(ctypes.Structure):
     _fields_ = [("debug", ctypes.c_int), ("chkbnds", ctypes.c_int), ("modeord", ctypes.c_int),
                 ("bin_size", ctypes.c_int * 3), ("max_subprob", ctypes.c_int), ("threads", ctypes.c_int),
-                ("sparse_max", ctypes.c_int), ("kerevalmeth", ctypes.c_int), ("reserved", ctypes.c_int * 6),
+                ("sparse_max", ctypes.c_int), ("kerevalmeth", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5),
                 ("upsampfac", ctypes.c_double)]
 
 
@@ -329,7 +330,7 @@ def _make_opts(opts: dict) -> nufft_opts:
 def opts_dict(o: nufft_opts) -> dict:
     """The tunable fields of an options struct, as keyword arguments for Plan / BatchPlan."""
     return {"bin_size": tuple(o.bin_size), "max_subprob": o.max_subprob, "threads": o.threads,
-            "sparse_max": o.sparse_max, "kerevalmeth": o.kerevalmeth, "upsampfac": o.upsampfac}
+            "sparse_max": o.sparse_max, "kerevalmeth": o.kerevalmeth, "kernel": o.kernel, "upsampfac": o.upsampfac}
 
 
 # --------------------------------------------------------------- torch layer

@@ -89,14 +89,20 @@ __device__ __forceinline__ DF df_exp_neg(DF x) {
   return DF{ldexpf(y.hi, ki), ldexpf(y.lo, ki)};
 }
 
-// The ES kernel (Eq. (ES)) exp(beta (sqrt(1 - z^2) - 1)) in double-float.
-__device__ __forceinline__ DF es_eval_df_z(DF z, DF beta) {
+// The ES kernel (Eq. (ES)) exp(beta (sqrt(1 - z^2) - 1)) in double-float; with cosh_kernel
+// its smooth variant (Remark in Sec. 7) as e^{beta (s - 1)} + e^{-beta (s + 1)}, both
+// exponents in [-2 beta, 0].
+__device__ __forceinline__ DF es_eval_df_z(DF z, DF beta, int cosh_kernel = 0) {
   const DF z2 = df_mul(z, z);
   const DF a = df_add(DF{1.0f, 0.0f}, DF{-z2.hi, -z2.lo});
   const DF s = df_sqrt(a);
   const DF x = df_mul(beta, df_add(s, DF{-1.0f, 0.0f}));
-  return df_exp_neg(x);
+  if (!cosh_kernel) return df_exp_neg(x);
+  const DF x2 = df_mul(beta, df_add(s, DF{1.0f, 0.0f}));
+  return df_add(df_exp_neg(x), df_exp_neg(DF{-x2.hi, -x2.lo}));
 }
-__device__ __forceinline__ DF es_eval_df(double z, DF beta) { return es_eval_df_z(df_of(z), beta); }
+__device__ __forceinline__ DF es_eval_df(double z, DF beta, int cosh_kernel = 0) {
+  return es_eval_df_z(df_of(z), beta, cosh_kernel);
+}
 
 }  // namespace nufft

@@ -7,6 +7,8 @@
 // paper notes (Remark in Sec. 7) that phi' is unbounded near z = +-1; the
 // factor 1 / sqrt(1 - z^2) is capped at 1e3 here, which only touches points
 // within ~5e-7 w/2 cells of a stencil edge, where phi itself is e^-beta.
+// With opts.kernel = 1 the plan uses the Remark's smooth variant instead,
+// whose derivative is bounded (es_eval_d).
 // The error of the derivative is a few times that of the values (aliased
 // frequencies near n are weighted by |k + m n| instead of |k|).
 //
@@ -25,16 +27,37 @@ struct GradOutT {
   T scale[3];                    // (2 / w) n_d / (2 pi) = -d z / d x_d
 };
 
-// k = phi(z) and dk = -phi'(z) = beta z / sqrt(1 - z^2) phi(z), the root capped below at 1e-3
-__device__ __forceinline__ void es_eval_d(float z, float kpar, float beta, float& k, float& dk) {
+// k = phi(z) and dk = -phi'(z).  ES: phi' = -beta z / sqrt(1 - z^2) phi(z), the root capped
+// below at 1e-3.  The smooth variant 2 e^-beta cosh(beta s), s = sqrt(1 - z^2) (Remark in
+// Sec. 7): phi = a + b with a = e^{beta (s - 1)}, b = e^{-beta (s + 1)}, and
+// -phi' = beta z (a - b) / s = 2 beta z e^-beta sinh(beta s) / s, bounded (-> 2 beta^2 z e^-beta
+// as s -> 0); for small beta s the quotient is taken from its series 2 beta e^-beta (1 + (beta s)^2 / 6).
+__device__ __forceinline__ void es_eval_d(float z, float kpar, float beta, int cosh_kernel, float& k, float& dk) {
   const float s = sqrtf(fmaxf(1.0f - z * z, 0.0f));
-  k = exp2f(kpar * (s - 1.0f));
-  dk = k * beta * z / fmaxf(s, 1e-3f);
+  if (!cosh_kernel) {
+    k = exp2f(kpar * (s - 1.0f));
+    dk = k * beta * z / fmaxf(s, 1e-3f);
+    return;
+  }
+  const float a = exp2f(kpar * (s - 1.0f)), b = exp2f(-kpar * (s + 1.0f));
+  k = a + b;
+  const float bs = beta * s;
+  const float q = bs > 0.05f ? (a - b) / s : 2.0f * beta * exp2f(-kpar) * (1.0f + bs * bs * (1.0f / 6.0f));
+  dk = beta * z * q;
 }
-__device__ __forceinline__ void es_eval_d(double z, double kpar, double beta, double& k, double& dk) {
+__device__ __forceinline__ void es_eval_d(double z, double kpar, double beta, int cosh_kernel, double& k,
+                                          double& dk) {
   const double s = sqrt(fmax(1.0 - z * z, 0.0));
-  k = exp(kpar * (s - 1.0));
-  dk = k * beta * z / fmax(s, 1e-3);
+  if (!cosh_kernel) {
+    k = exp(kpar * (s - 1.0));
+    dk = k * beta * z / fmax(s, 1e-3);
+    return;
+  }
+  const double a = exp(kpar * (s - 1.0)), b = exp(-kpar * (s + 1.0));
+  k = a + b;
+  const double bs = beta * s;
+  const double q = bs > 1e-3 ? (a - b) / s : 2.0 * beta * exp(-kpar) * (1.0 + bs * bs * (1.0 / 6.0));
+  dk = beta * z * q;
 }
 
 template <typename T>
@@ -49,13 +72,13 @@ __device__ __forceinline__ double beta_of<double>(double kpar) {
 }
 
 template <typename T, int W>
-__device__ __forceinline__ void point_weights_d(T v, int B, T kpar, T beta, int& ts, T* k, T* dk) {
+__device__ __forceinline__ void point_weights_d(T v, int B, T kpar, T beta, int cosh_kernel, int& ts, T* k, T* dk) {
   const int il = min((int)v, B - 1);
   const T f = v - T(il);
   const int s = stencil_step<W>(f);
   ts = il + s;
 #pragma unroll
-  for (int t = 0; t < W; ++t) es_eval_d(node_z<W>(t, s, f), kpar, beta, k[t], dk[t]);
+  for (int t = 0; t < W; ++t) es_eval_d(node_z<W>(t, s, f), kpar, beta, cosh_kernel, k[t], dk[t]);
 }
 
 // float: two blocks per SM (128 registers); double: one (the 1 + d complex
@@ -112,12 +135,12 @@ __global__ void __launch_bounds__(256, MinBlocksGrad<T>::value) k_interp_grad(Ge
       const Rec rq = rec[p0 + q];
       T k0[W], d0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights_d<T, W>(rq.v[0], g.B[0], kpar, beta, ts0, k0, d0);
+      point_weights_d<T, W>(rq.v[0], g.B[0], kpar, beta, g.kernel, ts0, k0, d0);
       T k1[(D > 1) ? W : 1], d1[(D > 1) ? W : 1];
       T f2 = T(0);
       int st2 = 0;
       if constexpr (D > 1) {
-        point_weights_d<T, W>(rq.v[1], g.B[1], kpar, beta, ts1, k1, d1);
+        point_weights_d<T, W>(rq.v[1], g.B[1], kpar, beta, g.kernel, ts1, k1, d1);
       } else {
         k1[0] = T(1);
         d1[0] = T(0);
@@ -158,7 +181,7 @@ __global__ void __launch_bounds__(256, MinBlocksGrad<T>::value) k_interp_grad(Ge
           }
         }
         T k2 = T(1), d2 = T(0);
-        if constexpr (D > 2) es_eval_d(node_z<W>(l2, st2, f2), kpar, beta, k2, d2);
+        if constexpr (D > 2) es_eval_d(node_z<W>(l2, st2, f2), kpar, beta, g.kernel, k2, d2);
         a.x = fma(b.x, k2, a.x);
         a.y = fma(b.y, k2, a.y);
         ax.x = fma(bx.x, k2, ax.x);
@@ -216,7 +239,7 @@ __global__ void __launch_bounds__(256) k_interp_grad_sparse(Geom g, T kpar, Sort
           const T v = dd == 0 ? v0 : (dd == 1 ? v1 : v2);
           const int il = min((int)v, g.B[dd] - 1);
           const T f = v - T(il);
-          es_eval_d(node_z<W>(t, stencil_step<W>(f), f), kpar, beta, wb[e], db[e]);
+          es_eval_d(node_z<W>(t, stencil_step<W>(f), f), kpar, beta, g.kernel, wb[e], db[e]);
         }
       }
       __syncwarp();

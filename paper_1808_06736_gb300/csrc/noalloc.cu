@@ -82,6 +82,7 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
   g.maxsub = kMaxSub;
   g.sparse_max = 32;
   g.horner = 0;
+  g.kernel = 0;
   int64_t ngrid = 1;
   for (int i = 0; i < 3; ++i) {
     int64_t v = i < dim ? n[i] : 1;

@@ -29,6 +29,7 @@ struct Geom {
   int maxsub;    // most points in one subproblem
   int sparse_max;  // subproblems with at most this many points take the per-warp path (0: none)
   int horner;      // 1: kernel values from the piecewise polynomial of Sec. 5.3 (horner_table)
+  int kernel;      // 0: the ES kernel, Eq. (ES); 1: 2 e^-beta cosh(beta sqrt(1 - z^2)) (Remark in Sec. 7)
 };
 
 // Bin ids run over super-blocks of sb[0] x sb[1] x sb[2] bins, dimension 1
@@ -259,6 +260,8 @@ void gl_positive_nodes(int p, double* q, double* wq);            // Gauss-Legend
 double sigma_from_opts(const nufft_opts& o);
 // w x (w + 4) monomial coefficients of Sec. 5.3's piecewise polynomial (see nufft_horner_coeffs);
 // computed once per (w, beta) and kept for the life of the process
-const double* horner_table(int w, double beta);
+const double* horner_table(int w, double beta, int kernel);
+// phi(z) on the host for kernel 0 (ES) or 1 (cosh variant); 0 outside [-1, 1]
+double kernel_value(double z, double beta, int kernel);
 
 }  // namespace nufft

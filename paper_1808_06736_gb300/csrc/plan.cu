@@ -177,17 +177,30 @@ void gauss_legendre_positive(int p, std::vector<double>& q, std::vector<double>&
   }
 }
 
+}  // namespace
+
+namespace nufft {
+double kernel_value(double z, double beta, int kernel) {
+  if (std::fabs(z) > 1.0) return 0.0;
+  const double s = std::sqrt(std::max(1.0 - z * z, 0.0));
+  if (kernel == 1) return 2.0 * std::exp(-beta) * std::cosh(beta * s);
+  return std::exp(beta * (s - 1.0));
+}
+}  // namespace nufft
+
+namespace {
+
 // Eq. (pk1) with Eq. (quad): p_k = 2 / (w phi^(alpha k)),
 // phi^(xi) = 2 sum_j w_j phi(q_j) cos(xi q_j) over the p positive nodes,
 // p = ceil(1.5 w + 2).  cos(alpha k q_j) by phase winding over k (a complex
 // multiply per step), re-anchored with a direct cos/sin every 256 steps.
-int correction_impl(int64_t N, int64_t n, int w, double beta, double* out) {
+int correction_impl(int64_t N, int64_t n, int w, double beta, double* out, int kernel = 0) {
   if (N < 1 || n < 1 || w < 2 || w > 16 || !out) return NUFFT_ERR_BAD_ARG;
   const int p = (int)std::ceil(1.5 * w + 2.0);
   std::vector<double> q, wq;
   gauss_legendre_positive(p, q, wq);
   std::vector<double> a(p);
-  for (int j = 0; j < p; ++j) a[j] = 2.0 * wq[j] * std::exp(beta * (std::sqrt(1.0 - q[j] * q[j]) - 1.0));
+  for (int j = 0; j < p; ++j) a[j] = 2.0 * wq[j] * nufft::kernel_value(q[j], beta, kernel);
   const double alpha = kPi * w / (double)n;
   const int64_t kmax = N - 1 - N / 2;   // largest k; |k| <= N/2
   const int64_t kabs = std::max<int64_t>(kmax, N / 2);
@@ -379,7 +392,7 @@ int nufft_choose_params_sigma(int dim, const int64_t* nmodes, double eps, int pr
 
 int nufft_horner_coeffs(int w, double beta, double* out) {
   if (w < 2 || w > 16 || !(beta > 0.0) || !out) return NUFFT_ERR_BAD_ARG;
-  const double* a = nufft::horner_table(w, beta);
+  const double* a = nufft::horner_table(w, beta, 0);
   std::memcpy(out, a, sizeof(double) * (size_t)w * (size_t)(w + 4));
   return NUFFT_OK;
 }
@@ -449,9 +462,11 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
   g.sparse_max = sparse_max_of(p->opts);
   g.horner = p->opts.kerevalmeth == 1 ? 1 : 0;
+  g.kernel = p->opts.kernel == 1 ? 1 : 0;
   choose_bins(g, p->dbl, p->opts);
   int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1)
+  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1 ||
+      p->opts.kernel < 0 || p->opts.kernel > 1)
     return fail(p, NUFFT_ERR_BAD_ARG);
 
   // device buffers owned by the plan
@@ -459,7 +474,8 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   size_t rs = p->dbl ? 8 : 4;
   for (int i = 0; i < 3; ++i) {
     std::vector<double> pk((size_t)p->N[i], 1.0);
-    if (i < dim && correction_impl(p->N[i], n[i], w, beta, pk.data()) != NUFFT_OK) return fail(p, NUFFT_ERR_BAD_ARG);
+    if (i < dim && correction_impl(p->N[i], n[i], w, beta, pk.data(), p->opts.kernel) != NUFFT_OK)
+      return fail(p, NUFFT_ERR_BAD_ARG);
     if (dev_alloc(&p->pk[i], (size_t)p->N[i] * rs) != cudaSuccess) return fail(p, NUFFT_ERR_ALLOC);
     if (p->dbl) {
       if (cudaMemcpy(p->pk[i], pk.data(), pk.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -711,6 +727,7 @@ int plan_estimate_bytes(int dim, const int64_t* nmodes, double eps, int prec, in
   g.maxsub = dbl ? 512 : 1024;
   g.sparse_max = 32;
   g.horner = 0;
+  g.kernel = 0;
   nufft_opts o;
   nufft_default_opts(&o);
   choose_bins(g, dbl, o);
@@ -734,7 +751,7 @@ void plan_choose_bins(Geom& g, bool dbl, const nufft_opts& o) { choose_bins(g, d
 // The kernel is analytic on every interval (its square-root branch points sit at the ends of
 // the support, where phi = e^-beta), so the monomial form stays well conditioned: the sum of
 // |coefficients| of an interval is about 1.
-static void horner_fit(int w, double beta, double* out) {
+static void horner_fit(int w, double beta, int kernel, double* out) {
   const int P = w + 4;
   const double pi = 3.14159265358979323846;
   std::vector<double> f((size_t)P), c((size_t)P), tm((size_t)P), tj((size_t)P), tn((size_t)P);
@@ -742,7 +759,7 @@ static void horner_fit(int w, double beta, double* out) {
     for (int k = 0; k < P; ++k) {
       const double sk = std::cos(pi * (k + 0.5) / P);
       const double z = (t - 0.5 * w + 0.5 * (sk + 1.0)) * 2.0 / w;
-      f[(size_t)k] = std::fabs(z) <= 1.0 ? std::exp(beta * (std::sqrt(std::max(1.0 - z * z, 0.0)) - 1.0)) : 0.0;
+      f[(size_t)k] = kernel_value(z, beta, kernel);
     }
     for (int j = 0; j < P; ++j) {
       double acc = 0.0;
@@ -767,15 +784,15 @@ static void horner_fit(int w, double beta, double* out) {
   }
 }
 
-const double* horner_table(int w, double beta) {
+const double* horner_table(int w, double beta, int kernel) {
   static std::mutex mu;
   static std::map<std::pair<int, double>, std::vector<double>> cache;
   std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_pair(w, beta);
+  auto key = std::make_pair(w + 100 * kernel, beta);
   auto it = cache.find(key);
   if (it == cache.end()) {
     std::vector<double> a((size_t)w * (size_t)(w + 4));
-    horner_fit(w, beta, a.data());
+    horner_fit(w, beta, kernel, a.data());
     it = cache.emplace(key, std::move(a)).first;
   }
   return it->second.data();
@@ -1029,6 +1046,7 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
   g.sparse_max = sparse_max_of(p->opts);
   g.horner = p->opts.kerevalmeth == 1 ? 1 : 0;
+  g.kernel = p->opts.kernel == 1 ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
     int64_t mx = 1;
     for (int t = 0; t < B; ++t) mx = std::max(mx, n[(size_t)t * 3 + i]);
@@ -1112,7 +1130,8 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   std::vector<double> pkh((size_t)pkoff, 1.0);
   for (int t = 0; t < B; ++t)
     for (int i = 0; i < dim; ++i)
-      if (correction_impl(p->hg[t].N[i], p->hg[t].n[i], p->w, p->beta, &pkh[p->hg[t].pkoff[i]]) != NUFFT_OK)
+      if (correction_impl(p->hg[t].N[i], p->hg[t].n[i], p->w, p->beta, &pkh[p->hg[t].pkoff[i]], p->opts.kernel) !=
+          NUFFT_OK)
         return batch_fail(p, NUFFT_ERR_BAD_ARG);
   const size_t rs = p->dbl ? 8 : 4;
   if (dev_alloc(&p->grid, (size_t)p->total_grid * p->csize) != cudaSuccess ||
@@ -1144,7 +1163,8 @@ int nufft_batch_makeplan(int type, int dim, int B, const int64_t* nmodes, int is
   okc &= cudaMemset(p->small, 0, sizeof(int) * 4) == cudaSuccess;
   if (!okc) return batch_fail(p, NUFFT_ERR_CUDA);
   int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1)
+  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1 ||
+      p->opts.kernel < 0 || p->opts.kernel > 1)
     return batch_fail(p, NUFFT_ERR_BAD_ARG);
   cudaError_t e = (type == 1) ? spread_config(p->dbl, g, threads, &p->cfg) : interp_config(p->dbl, g, threads, &p->cfg);
   if (e != cudaSuccess) return batch_fail(p, NUFFT_ERR_CUDA);

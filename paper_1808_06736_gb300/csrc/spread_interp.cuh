@@ -70,6 +70,20 @@ __device__ __forceinline__ float es_eval(float z, float kpar) {
 __device__ __forceinline__ double es_eval(double z, double kpar) {
   return exp(kpar * (sqrt(fmax(1.0 - z * z, 0.0)) - 1.0));
 }
+// The smooth variant 2 e^-beta cosh(beta s), s = sqrt(1 - z^2) (Remark in Sec. 7),
+// as e^{beta (s - 1)} + e^{-beta (s + 1)}.
+__device__ __forceinline__ float es_cosh_eval(float z, float kpar) {
+  const float s = sqrtf(fmaxf(1.0f - z * z, 0.0f));
+  return exp2f(kpar * (s - 1.0f)) + exp2f(-kpar * (s + 1.0f));
+}
+__device__ __forceinline__ double es_cosh_eval(double z, double kpar) {
+  const double s = sqrt(fmax(1.0 - z * z, 0.0));
+  return exp(kpar * (s - 1.0)) + exp(-kpar * (s + 1.0));
+}
+template <typename T>
+__device__ __forceinline__ T kernel_eval(T z, T kpar, int cosh_kernel) {
+  return cosh_kernel ? es_cosh_eval(z, kpar) : es_eval(z, kpar);
+}
 
 // The stencil of a coordinate u = cell + f starts at ceil(u - w/2), i.e. at
 // cell - floor(w/2) + step with step = [f > 0] (w even) or [f > 1/2] (w odd);
@@ -94,6 +108,7 @@ struct KEval {
   static constexpr int NC = W + 4;
   T kpar;
   int horner;
+  int cosh_kernel;  // formula of the smooth variant (Remark in Sec. 7) instead of Eq. (ES)
   T a[W * NC];
 };
 
@@ -117,7 +132,7 @@ __device__ __forceinline__ T kernel_node(const KEval<T, W>& ke, int t, int step,
     for (int m = NC - 2; m >= 0; --m) y = fma(y, x, a[m]);
     return y;
   }
-  return es_eval(node_z<W>(t, step, f), ke.kpar);
+  return kernel_eval(node_z<W>(t, step, f), ke.kpar, ke.cosh_kernel);
 }
 
 // kernel values of all W nodes of a coordinate
@@ -134,7 +149,7 @@ __device__ __forceinline__ void kernel_row(const KEval<T, W>& ke, int step, T f,
       for (int t = 0; t < W; ++t) k[t] = fma(k[t], x, ke.a[t * NC + m]);
   } else {
 #pragma unroll
-    for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, step, f), ke.kpar);
+    for (int t = 0; t < W; ++t) k[t] = kernel_eval(node_z<W>(t, step, f), ke.kpar, ke.cosh_kernel);
   }
 }
 
@@ -634,7 +649,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, con
 // the scale is undone exactly on output).
 // kernel values along one dimension in double-float (see point_weights)
 template <int W>
-__device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int& ts, DF* k) {
+__device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int cosh_kernel, int& ts, DF* k) {
   const int il = min((int)v, B - 1);
   const double f = v - double(il);
   const int s = stencil_step<W>(f);
@@ -645,7 +660,7 @@ __device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int& 
   for (int t = 0; t < W; ++t) {
     // z = (t - floor(w/2) + step - f) 2 / w in double-float
     const DF z = df_mul(df_add(DF{(float)(t - W / 2 + s), 0.0f}, DF{-fd.hi, -fd.lo}), scale);
-    k[t] = es_eval_df_z(z, beta);
+    k[t] = es_eval_df_z(z, beta, cosh_kernel);
   }
 }
 
@@ -717,12 +732,12 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
       const Rec rq = rec[p0 + q];
       DF k0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights_df<W>(rq.v[0], g.B[0], bdf, ts0, k0);
+      point_weights_df<W>(rq.v[0], g.B[0], bdf, ke.cosh_kernel, ts0, k0);
       DF k1[(D > 1) ? W : 1];
       double f2 = 0.0;
       int st2 = 0;
       if constexpr (D > 1) {
-        point_weights_df<W>(rq.v[1], g.B[1], bdf, ts1, k1);
+        point_weights_df<W>(rq.v[1], g.B[1], bdf, ke.cosh_kernel, ts1, k1);
       } else {
         k1[0] = DF{1.0f, 0.0f};
       }
@@ -762,7 +777,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
           df_mac(bi, si, k1[l1]);
         }
         DF k2 = {1.0f, 0.0f};
-        if constexpr (D > 2) k2 = es_eval_df(node_z<W>(l2, st2, f2), bdf);
+        if constexpr (D > 2) k2 = es_eval_df(node_z<W>(l2, st2, f2), bdf, ke.cosh_kernel);
         df_mac(ar, df_norm(br), k2);
         df_mac(ai, df_norm(bi), k2);
       }
@@ -1035,7 +1050,8 @@ inline KEval<T, W> make_keval(const Geom& g, double beta) {
   KEval<T, W> ke;
   ke.kpar = kernel_param<T>(beta);
   ke.horner = g.horner ? 1 : 0;
-  const double* a = g.horner ? horner_table(W, beta) : nullptr;
+  ke.cosh_kernel = g.kernel == 1 ? 1 : 0;
+  const double* a = g.horner ? horner_table(W, beta, ke.cosh_kernel) : nullptr;
   for (int i = 0; i < W * KEval<T, W>::NC; ++i) ke.a[i] = a ? T(a[i]) : T(0);
   return ke;
 }

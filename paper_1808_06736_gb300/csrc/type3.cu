@@ -314,9 +314,11 @@ int setpts_t(nufft_plan3 p, int64_t M, const void* x, const void* y, const void*
   g.maxsub = p->opts.max_subprob > 0 ? std::min(p->opts.max_subprob, 8192) : (p->dbl ? 512 : 1024);
   g.sparse_max = p->opts.sparse_max < 0 ? 0 : (p->opts.sparse_max == 0 ? 32 : std::min(p->opts.sparse_max, 32));
   g.horner = p->opts.kerevalmeth == 1 ? 1 : 0;
+  g.kernel = p->opts.kernel == 1 ? 1 : 0;
   plan_choose_bins(g, p->dbl, p->opts);
   const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1)
+  if (threads % 32 != 0 || threads > 256 || p->opts.kerevalmeth < 0 || p->opts.kerevalmeth > 1 ||
+      p->opts.kernel < 0 || p->opts.kernel > 1)
     return NUFFT_ERR_BAD_ARG;
   if (spread_config(p->dbl, g, threads, &p->scfg) != cudaSuccess) return NUFFT_ERR_CUDA;
   if (!ensure(p->gridcap, ngrid, {{&p->grid, p->cs}})) return NUFFT_ERR_ALLOC;
@@ -382,7 +384,7 @@ int setpts_t(nufft_plan3 p, int64_t M, const void* x, const void* y, const void*
     gl_positive_nodes(gl.p, q.data(), wq.data());
     for (int j = 0; j < gl.p; ++j) {
       gl.q[j] = q[(size_t)j];
-      gl.wf[j] = wq[(size_t)j] * std::exp(p->beta * (std::sqrt(1.0 - q[(size_t)j] * q[(size_t)j]) - 1.0));
+      gl.wf[j] = wq[(size_t)j] * kernel_value(q[(size_t)j], p->beta, p->g.kernel);
       gl.qf[j] = (float)gl.q[j];
       gl.wff[j] = (float)gl.wf[j];
     }

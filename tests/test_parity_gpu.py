@@ -262,7 +262,8 @@ GRAD_SIZES = {1: ([400], 3000), 2: ([40, 36], 6000), 3: ([16, 14, 12], 8000)}
 @pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex64, 1e-3), (np.complex128, 1e-9)])
 @pytest.mark.parametrize("d", [1, 2, 3])
 @pytest.mark.parametrize("density", ["dense", "sparse"])
-def test_execute_grad_against_direct_sum_derivative(pkg, oracle_mod, cdtype, eps, d, density):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_execute_grad_against_direct_sum_derivative(pkg, oracle_mod, cdtype, eps, d, density, kernel):
     """nufft_execute_grad: values as nufft_execute, and dc_j/dx_{j,d} against the FP64
     derivative of the exact sum, sum_k f_k (i isign k_d) exp(i isign k.x_j).
 
@@ -282,7 +283,7 @@ def test_execute_grad_against_direct_sum_derivative(pkg, oracle_mod, cdtype, eps
     tdt = torch.complex64 if cdtype == np.complex64 else torch.complex128
     rdt = np.float32 if cdtype == np.complex64 else np.float64
     isign = -1
-    p = pkg.Plan(2, Ns, eps=eps, isign=isign, dtype=tdt, device=dev)
+    p = pkg.Plan(2, Ns, eps=eps, isign=isign, dtype=tdt, device=dev, kernel=kernel)
     p.setpts(*[torch.from_numpy(np.ascontiguousarray(v, dtype=rdt)).to(dev) for v in xs])
     fd = torch.from_numpy(np.ascontiguousarray(f, dtype=cdtype)).to(dev)
     c, dc = p.execute_grad(fd)
@@ -401,3 +402,33 @@ def test_timings_before_execute_leave_no_error(pkg):
     assert all(v >= 0 for v in t)
     assert p.status() == 0
     p.close()
+
+
+# The smooth kernel 2 e^-beta cosh(beta sqrt(1 - z^2)) of the Remark in Sec. 7 (opts.kernel = 1,
+# same w and beta, its own correction factors): against O2 with that kernel (rounding budget),
+# against the exact sums (10 eps), and with the piecewise polynomial fitted to it.
+COSH_CASES = [(np.complex64, 1e-5), (np.complex64, 1e-3), (np.complex128, 1e-9), (np.complex128, 1e-12)]
+
+
+@pytest.mark.parametrize("cdtype,eps", COSH_CASES)
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_parity_cosh_kernel(pkg, oracle_mod, cdtype, eps, d):
+    Ns, M = SIZES[d]
+    xs, c, f = case_inputs(d, Ns, M, "uniform", cdtype, seed=6000 + 10 * d)
+    x64 = [v.astype(np.float64) for v in xs]
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    g1, info = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, kernel=1)
+    assert info["w"] == w and info["n"] == ns
+    g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, kernel=1)
+    o2_1 = oracle_mod.type1(x64, c, 1, Ns, w=w, beta=beta, ns=ns, kernel="cosh")
+    o2_2 = oracle_mod.type2(x64, f, -1, Ns, w=w, beta=beta, ns=ns, kernel="cosh")
+    assert oracle_mod.rel_l2(g1[0], o2_1) <= TOL_SAME[cdtype]
+    assert oracle_mod.rel_l2(g2[0], o2_2) <= TOL_SAME[cdtype]
+    o1_1 = oracle_mod.direct_type1(x64, c, 1, Ns)
+    o1_2 = oracle_mod.direct_type2(x64, f, -1, Ns)
+    assert oracle_mod.rel_l2(g1[0], o1_1) <= 10 * eps
+    assert oracle_mod.rel_l2(g2[0], o1_2) <= 10 * eps
+    h1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype, kernel=1, kerevalmeth=1)
+    h2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, kernel=1, kerevalmeth=1)
+    assert oracle_mod.rel_l2(h1[0], o1_1) <= 10 * eps
+    assert oracle_mod.rel_l2(h2[0], o1_2) <= 10 * eps
