@@ -78,7 +78,9 @@ typedef struct {
                          use the formula. */
   int kernel;         /* 0: the ES kernel, Eq. (ES); 1: its smooth variant 2 e^-beta cosh(beta sqrt(1 - z^2))
                          (Remark in Sec. 7: within e^-beta of ES, bounded derivatives; same w and beta, its
-                         own correction factors), for point gradients (nufft_execute_grad) */
+                         own correction factors), for point gradients (nufft_execute_grad).  The spread
+                         and interp kernels evaluate it through its piecewise polynomial (Sec. 5.3),
+                         the gradient and complex128 interpolation kernels through its formula */
   int reserved[5];    /* set to zero */
   double upsampfac;   /* fine grid / modes per dimension, sigma: 2 (0 means 2) or 1.25 (smaller FFTs and
                          grids, wider kernel: w from the slope of Eq. (ESerr), beta from Eq. (gam); more
@@ -334,6 +336,18 @@ int nufft3_plan_info(nufft_plan3 plan, int* w, double* beta, int64_t* n, double*
 int nufft3_get_status(nufft_plan3 plan);
 /* Free the plan (NULL is allowed).  Synchronises its stream first. */
 int nufft3_destroy(nufft_plan3 plan);
+
+/* ------------------------------------------------------------ unit peaks
+ * Microbenchmarks of the units that bound the spread and interp kernels, for
+ * their rooflines, run on the current device and enqueued on stream (a
+ * cudaStream_t; the call synchronises it): out[0] FP32 FMA throughput in
+ * TFLOP/s, out[1] FP64 FMA in TFLOP/s, out[2] special-function operations
+ * (exp2 and reciprocal square root) in G ops/s, out[3] 32-bit shared-memory
+ * atomic adds per second with conflict-free addresses.  Each figure is the
+ * second of two launches of 8 blocks of 256 threads per SM running 8
+ * independent chains per thread; about 3 ms in all.  n >= 4.  Returns
+ * NUFFT_OK, NUFFT_ERR_BAD_ARG, NUFFT_ERR_ALLOC or NUFFT_ERR_CUDA. */
+int nufft_measure_peaks(void* stream, double* out, int n);
 
 /* ------------------------------------------------------------ no allocation
  * nufft_spread_noalloc -- the spreading step of a complex64 type-1 transform

@@ -19,7 +19,7 @@ __all__ = [
     "Plan", "NufftError", "nufft_opts", "nufft_default_opts", "nufft_makeplan", "nufft_setpts",
     "nufft_execute", "nufft_execute_grad", "nufft_destroy", "nufft_get_status", "nufft_get_timings", "nufft_plan_info",
     "nufft_strerror", "nufft_choose_params", "nufft_choose_params_sigma", "nufft_correction_factors", "nufft_next235",
-    "nufft_horner_coeffs",
+    "nufft_horner_coeffs", "nufft_measure_peaks",
     "nufft_spread_noalloc", "library_path", "BatchPlan", "nufft_batch_makeplan", "nufft_batch_setpts",
     "nufft_batch_execute", "nufft_batch_get_status", "nufft_batch_destroy", "nufft_tune", "nufft_batch_tune",
     "nufft_tune_candidates", "opts_dict", "tune_plan", "tune_batch", "Plan3", "nufft3_makeplan", "nufft3_setpts",
@@ -100,6 +100,7 @@ def _L():
     lib.nufft_batch_tune.argtypes = [i32, i32, i32, pi64, i32, dbl, i32, pi64, vp, vp, vp, vp, vp, vp, i32,
                                      ctypes.POINTER(nufft_opts), pd, pd]
     lib.nufft_tune_candidates.argtypes = [i32, i32, i32, ctypes.POINTER(i32), i32]
+    lib.nufft_measure_peaks.argtypes = [vp, pd, i32]
     lib.nufft3_makeplan.argtypes = [i32, i32, dbl, i32, vp, ctypes.POINTER(nufft_opts), ctypes.POINTER(vp)]
     lib.nufft3_setpts.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, vp]
     lib.nufft3_execute.argtypes = [vp, vp, vp]
@@ -279,6 +280,14 @@ def nufft_batch_tune(type_: int, dim: int, nmodes, isign: int, eps: float, prec:
                                vp(x or 0), vp(y or 0), vp(z or 0), vp(inp or 0), vp(out or 0), vp(stream or 0),
                                int(reps), ctypes.byref(o), ctypes.byref(b), ctypes.byref(d))
     return st, o, b.value, d.value
+
+
+def nufft_measure_peaks(stream: int | None = None):
+    """(status, {fp32_tflops, fp64_tflops, sfu_gops, smem_atomics_per_s}) on the current device."""
+    buf = (ctypes.c_double * 4)()
+    st = _L().nufft_measure_peaks(ctypes.c_void_p(stream or 0), buf, 4)
+    keys = ("fp32_tflops", "fp64_tflops", "sfu_gops", "smem_atomics_per_s")
+    return st, (dict(zip(keys, list(buf))) if st == 0 else None)
 
 
 def nufft3_makeplan(dim: int, isign: int, eps: float, prec: int, stream: int | None, opts: nufft_opts | None):

@@ -70,20 +70,6 @@ __device__ __forceinline__ float es_eval(float z, float kpar) {
 __device__ __forceinline__ double es_eval(double z, double kpar) {
   return exp(kpar * (sqrt(fmax(1.0 - z * z, 0.0)) - 1.0));
 }
-// The smooth variant 2 e^-beta cosh(beta s), s = sqrt(1 - z^2) (Remark in Sec. 7),
-// as e^{beta (s - 1)} + e^{-beta (s + 1)}.
-__device__ __forceinline__ float es_cosh_eval(float z, float kpar) {
-  const float s = sqrtf(fmaxf(1.0f - z * z, 0.0f));
-  return exp2f(kpar * (s - 1.0f)) + exp2f(-kpar * (s + 1.0f));
-}
-__device__ __forceinline__ double es_cosh_eval(double z, double kpar) {
-  const double s = sqrt(fmax(1.0 - z * z, 0.0));
-  return exp(kpar * (s - 1.0)) + exp(-kpar * (s + 1.0));
-}
-template <typename T>
-__device__ __forceinline__ T kernel_eval(T z, T kpar, int cosh_kernel) {
-  return cosh_kernel ? es_cosh_eval(z, kpar) : es_eval(z, kpar);
-}
 
 // The stencil of a coordinate u = cell + f starts at ceil(u - w/2), i.e. at
 // cell - floor(w/2) + step with step = [f > 0] (w even) or [f > 1/2] (w odd);
@@ -102,7 +88,12 @@ __device__ __forceinline__ T node_z(int t, int step, T f) {
 // set, the piecewise polynomial of Sec. 5.3 (w intervals, degree w + 3,
 // a[t * NC + m] the coefficient of s^m on interval t).  Kernels take it as a
 // __grid_constant__ parameter, so in the unrolled Horner loops each coefficient
-// is a constant-bank operand of its FMA.
+// is a constant-bank operand of its FMA.  The formula branch evaluates Eq. (ES)
+// only: plans with the smooth variant (Remark in Sec. 7) take their kernel
+// values from its piecewise polynomial here (make_keval sets horner), which
+// keeps a second formula, and the registers it costs, out of these kernels;
+// the double-float interpolation and the gradient kernels evaluate the
+// variant's formula (cosh_kernel).
 template <typename T, int W>
 struct KEval {
   static constexpr int NC = W + 4;
@@ -132,7 +123,7 @@ __device__ __forceinline__ T kernel_node(const KEval<T, W>& ke, int t, int step,
     for (int m = NC - 2; m >= 0; --m) y = fma(y, x, a[m]);
     return y;
   }
-  return kernel_eval(node_z<W>(t, step, f), ke.kpar, ke.cosh_kernel);
+  return es_eval(node_z<W>(t, step, f), ke.kpar);
 }
 
 // kernel values of all W nodes of a coordinate
@@ -149,7 +140,7 @@ __device__ __forceinline__ void kernel_row(const KEval<T, W>& ke, int step, T f,
       for (int t = 0; t < W; ++t) k[t] = fma(k[t], x, ke.a[t * NC + m]);
   } else {
 #pragma unroll
-    for (int t = 0; t < W; ++t) k[t] = kernel_eval(node_z<W>(t, step, f), ke.kpar, ke.cosh_kernel);
+    for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, step, f), ke.kpar);
   }
 }
 
@@ -1049,9 +1040,9 @@ template <typename T, int W>
 inline KEval<T, W> make_keval(const Geom& g, double beta) {
   KEval<T, W> ke;
   ke.kpar = kernel_param<T>(beta);
-  ke.horner = g.horner ? 1 : 0;
   ke.cosh_kernel = g.kernel == 1 ? 1 : 0;
-  const double* a = g.horner ? horner_table(W, beta, ke.cosh_kernel) : nullptr;
+  ke.horner = (g.horner || ke.cosh_kernel) ? 1 : 0;
+  const double* a = ke.horner ? horner_table(W, beta, ke.cosh_kernel) : nullptr;
   for (int i = 0; i < W * KEval<T, W>::NC; ++i) ke.a[i] = a ? T(a[i]) : T(0);
   return ke;
 }

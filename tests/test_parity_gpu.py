@@ -405,8 +405,10 @@ def test_timings_before_execute_leave_no_error(pkg):
 
 
 # The smooth kernel 2 e^-beta cosh(beta sqrt(1 - z^2)) of the Remark in Sec. 7 (opts.kernel = 1,
-# same w and beta, its own correction factors): against O2 with that kernel (rounding budget),
-# against the exact sums (10 eps), and with the piecewise polynomial fitted to it.
+# same w and beta, its own correction factors): against the exact sums (10 eps) and against O2
+# with that kernel.  The tiled and per-warp kernels take its values from its piecewise
+# polynomial (the complex128 interpolation and the gradient kernels from its formula), so the
+# bar against O2 is the rounding budget plus the polynomial's error: max(budget, eps).
 COSH_CASES = [(np.complex64, 1e-5), (np.complex64, 1e-3), (np.complex128, 1e-9), (np.complex128, 1e-12)]
 
 
@@ -422,8 +424,9 @@ def test_parity_cosh_kernel(pkg, oracle_mod, cdtype, eps, d):
     g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, kernel=1)
     o2_1 = oracle_mod.type1(x64, c, 1, Ns, w=w, beta=beta, ns=ns, kernel="cosh")
     o2_2 = oracle_mod.type2(x64, f, -1, Ns, w=w, beta=beta, ns=ns, kernel="cosh")
-    assert oracle_mod.rel_l2(g1[0], o2_1) <= TOL_SAME[cdtype]
-    assert oracle_mod.rel_l2(g2[0], o2_2) <= TOL_SAME[cdtype]
+    tol = max(TOL_SAME[cdtype], eps)
+    assert oracle_mod.rel_l2(g1[0], o2_1) <= tol
+    assert oracle_mod.rel_l2(g2[0], o2_2) <= tol
     o1_1 = oracle_mod.direct_type1(x64, c, 1, Ns)
     o1_2 = oracle_mod.direct_type2(x64, f, -1, Ns)
     assert oracle_mod.rel_l2(g1[0], o1_1) <= 10 * eps

@@ -160,3 +160,18 @@ def test_type3_large_sampled(pkg, oracle_mod):
     ref = oracle_mod.direct_type3(xs, c, 1, [v[idx] for v in ss])
     assert oracle_mod.rel_l2(f[idx], ref) <= 10 * eps
     del torch
+
+
+@pytest.mark.parametrize("opts", [{"kerevalmeth": 1}, {"kernel": 1}, {"kernel": 1, "kerevalmeth": 1},
+                                  {"upsampfac": 1.25}])
+def test_type3_plan_options(pkg, oracle_mod, opts):
+    """The plan options reach both steps of type 3 (the spreading grid and the inner type 2):
+    the piecewise polynomial kernel, the smooth cosh kernel, and sigma = 5/4 (n_i then follows
+    Eq. (ng) with sigma = 5/4).  complex128, 2D, against the exact sum."""
+    cd, eps = np.complex128, 1e-9
+    xs, ss, c = inputs(2, 4000, 3000, 5.0, 14.0, cd, 995)
+    f, info = run3(pkg, xs, ss, c, eps, 1, cd, **opts)
+    sigma = opts.get("upsampfac", 2.0)
+    P = oracle_mod.type3_params(eps, xs, ss, sigma=sigma)
+    assert info["n"] == P["ns"] and info["w"] == P["w"]
+    assert oracle_mod.rel_l2(f, oracle_mod.direct_type3(xs, c, 1, ss)) <= 10 * eps
