@@ -655,7 +655,7 @@ __device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int c
   }
 }
 
-template <int D, int W>
+template <int D, int W, bool COSH>
 __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_constant__ KEval<double, W> ke, Sorted s, const double2* __restrict__ grid,
                                                       double2* __restrict__ c, int* __restrict__ work, BatchTable bt) {
   using Rec = typename Traits<double>::Rec;
@@ -723,12 +723,12 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
       const Rec rq = rec[p0 + q];
       DF k0[W];
       int ts0, ts1 = 0, ts2 = 0;
-      point_weights_df<W>(rq.v[0], g.B[0], bdf, ke.cosh_kernel, ts0, k0);
+      point_weights_df<W>(rq.v[0], g.B[0], bdf, COSH, ts0, k0);
       DF k1[(D > 1) ? W : 1];
       double f2 = 0.0;
       int st2 = 0;
       if constexpr (D > 1) {
-        point_weights_df<W>(rq.v[1], g.B[1], bdf, ke.cosh_kernel, ts1, k1);
+        point_weights_df<W>(rq.v[1], g.B[1], bdf, COSH, ts1, k1);
       } else {
         k1[0] = DF{1.0f, 0.0f};
       }
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
           df_mac(bi, si, k1[l1]);
         }
         DF k2 = {1.0f, 0.0f};
-        if constexpr (D > 2) k2 = es_eval_df(node_z<W>(l2, st2, f2), bdf, ke.cosh_kernel);
+        if constexpr (D > 2) k2 = es_eval_df(node_z<W>(l2, st2, f2), bdf, COSH);
         df_mac(ar, df_norm(br), k2);
         df_mac(ai, df_norm(bi), k2);
       }
@@ -779,14 +779,15 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
   }
 }
 
-// the tiled interpolation kernel for each precision
+// the tiled interpolation kernel for each precision (complex128: one instance per
+// kernel formula, so the ES path carries no code for the smooth variant)
 template <typename T, int D, int W>
 struct InterpKernel {
-  static constexpr auto value = k_interp<T, D, W>;
+  static auto get(bool) { return k_interp<T, D, W>; }
 };
 template <int D, int W>
 struct InterpKernel<double, D, W> {
-  static constexpr auto value = k_interp_df<D, W>;
+  static auto get(bool cosh) { return cosh ? k_interp_df<D, W, true> : k_interp_df<D, W, false>; }
 };
 
 // ------------------------------------------------- sparse subproblems
@@ -1076,7 +1077,7 @@ template <typename T, int D, int W>
 cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* grid, void* c,
                        int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
                        const BatchTable& bt) {
-  auto kern = InterpKernel<T, D, W>::value;
+  auto kern = InterpKernel<T, D, W>::get(g.kernel == 1);
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
