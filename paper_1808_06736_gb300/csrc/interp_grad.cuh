@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256, MinBlocksGrad<T>::value) k_interp_grad(Ge
   using Rec = typename Traits<T>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_INTERP];
-  __shared__ int s_sub;
+  __shared__ int s_sub, s_nslots;
 
   const int ntile = g.ntile, maxsub = g.maxsub;
   C* tile = reinterpret_cast<C*>(smem);
@@ -128,10 +128,11 @@ __global__ void __launch_bounds__(256, MinBlocksGrad<T>::value) k_interp_grad(Ge
     cp_async_commit();
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) stage_point<T, D, W, NRES_INTERP>(g, rec[p0 + q], q, st, hist);
     cp_async_wait_all();
-    bucket_order<T, D, NRES_INTERP>(cnt, st, hist);
+    const int nslots = bucket_order<T, D, NRES_INTERP, true>(cnt, st, hist, &s_nslots);
 
-    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const int q = st.order[sl];
+      if (q == kEmptySlot) continue;
       const Rec rq = rec[p0 + q];
       T k0[W], d0[W];
       int ts0, ts1 = 0, ts2 = 0;

@@ -279,11 +279,13 @@ namespace nufft {
 
 size_t spread_smem_bytes(bool dbl, const Geom& g, int) {
   size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8;
+  // the spread's point order is gapless: res, rank and order of maxsub entries each
   return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc + (size_t)g.maxsub * 3 * 2;
 }
 size_t interp_smem_bytes(bool dbl, const Geom& g, int) {
   size_t cc = dbl ? 16 : 8;
-  return (size_t)g.ntile * cc + (size_t)g.maxsub * 3 * 2;
+  // res, rank, the slot order (2 maxsub) and the round starts of the aligned point order
+  return (size_t)g.ntile * cc + (size_t)g.maxsub * 5 * 2;
 }
 
 static cudaError_t si_dispatch(bool spread, bool dbl, const Geom& g, double beta, const Sorted& s,

@@ -219,15 +219,19 @@ constexpr int NRES_SPREAD = 32;
 // point is processed); shared memory keeps only the ordering state, so that
 // more thread blocks fit on an SM.
 template <typename T, int D>
+// The spread's gapless order uses res, rank and the first maxsub entries of order
+// only, and its shared memory holds just those (3 maxsub); the interpolation's
+// aligned order needs all of it (5 maxsub).
 struct Stage {
-  unsigned short* res;   // [maxsub] bank group of the stencil corner
-  unsigned short* rank;  // [maxsub] rank within its group
-  unsigned short* order; // [maxsub] processing order
+  unsigned short* res;     // [maxsub] bank group of the stencil corner
+  unsigned short* rank;    // [maxsub] rank within its group
+  unsigned short* order;   // [2 maxsub] processing order by slot (0xFFFF: empty slot)
+  unsigned short* rstart;  // [maxsub] first slot of each round
 };
 
 template <typename T, int D>
-__host__ __device__ inline size_t stage_bytes(int maxsub) {
-  return (size_t)maxsub * 3 * sizeof(unsigned short);
+__host__ __device__ inline size_t stage_bytes(int maxsub, bool aligned = true) {
+  return (size_t)maxsub * (aligned ? 5 : 3) * sizeof(unsigned short);
 }
 
 template <typename T, int D>
@@ -236,8 +240,10 @@ __device__ __forceinline__ Stage<T, D> carve_stage(unsigned char* p, int maxsub)
   s.res = reinterpret_cast<unsigned short*>(p);
   s.rank = s.res + maxsub;
   s.order = s.rank + maxsub;
+  s.rstart = s.order + 2 * maxsub;
   return s;
 }
+constexpr unsigned short kEmptySlot = 0xFFFF;
 
 // Decode a bin index into its per-dimension tile origin (bin origin - floor(w/2)).
 __device__ __forceinline__ void tile_origin(const Geom& g, int bin, int* org) {
@@ -266,24 +272,77 @@ __device__ __forceinline__ void stage_point(const Geom& g, const typename Traits
   st.rank[q] = (unsigned short)atomicAdd(&hist[rr], 1);
 }
 
-// Round-robin order over the bank groups: round r takes the r-th point of
-// every group that has more than r points, groups in increasing order.  The
-// point of group b with rank r lands at
-//   sum_g min(size_g, r) + #{g < b : size_g > r}.
-template <typename T, int D, int NRES>
-__device__ __forceinline__ void bucket_order(int cnt, Stage<T, D>& st, const int* hist) {
+// Processing order over the bank groups.  Round r takes the r-th point of every group
+// that has more than r points, groups in increasing order, so the points of one round
+// lie in different bank groups.
+//  * ALIGNED = false: rounds follow each other without gaps; the point of group b with
+//    rank r lands at sum_g min(size_g, r) + #{g < b : size_g > r}.  Returns cnt.
+//  * ALIGNED = true: rounds are packed whole into consecutive groups of NRES slots (a
+//    half-warp for the interpolation's 8-byte loads): a round that does not fit in what
+//    is left of the current slot group starts the next one, and the slots it leaves stay
+//    empty (kEmptySlot).  A slot group then never holds two points of one bank group from
+//    one round, which gapless packing does at the tail of uneven groups.  Each gap is
+//    smaller than the round that did not fit, so there are fewer than 2 cnt slots.
+//    Returns the number of slots.
+// The interpolation kernels take the aligned order (1.6-2.8 % faster on the 3D benchmark
+// workload); the spread keeps the gapless one (its aligned variant measured 11 % slower).
+// Synchronises the block.
+template <typename T, int D, int NRES, bool ALIGNED>
+__device__ __forceinline__ int bucket_order(int cnt, Stage<T, D>& st, const int* hist, int* s_nslots) {
   __syncthreads();
   int sz[NRES];
+  int maxsz = 0;
 #pragma unroll
-  for (int b = 0; b < NRES; ++b) sz[b] = hist[b];
+  for (int b = 0; b < NRES; ++b) {
+    sz[b] = hist[b];
+    maxsz = max(maxsz, sz[b]);
+  }
+  if constexpr (!ALIGNED) {
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const int r = st.rank[q], b = st.res[q];
+      int pos = 0;
+#pragma unroll
+      for (int g = 0; g < NRES; ++g) pos += min(sz[g], r) + ((g < b && sz[g] > r) ? 1 : 0);
+      st.order[pos] = (unsigned short)q;
+    }
+    __syncthreads();
+    return cnt;
+  }
+  for (int r = threadIdx.x; r < maxsz; r += blockDim.x) {  // round sizes (maxsz <= cnt)
+    int k = 0;
+#pragma unroll
+    for (int b = 0; b < NRES; ++b) k += sz[b] > r ? 1 : 0;
+    st.rstart[r] = (unsigned short)k;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int slot = 0, fill = 0;  // fill = slot mod NRES
+    for (int r = 0; r < maxsz; ++r) {
+      const int k = st.rstart[r];
+      if (fill + k > NRES) {
+        slot += NRES - fill;
+        fill = 0;
+      }
+      st.rstart[r] = (unsigned short)slot;
+      slot += k;
+      fill += k;
+      if (fill == NRES) fill = 0;
+    }
+    *s_nslots = slot;
+  }
+  __syncthreads();
+  const int nslots = *s_nslots;
+  for (int i = threadIdx.x; i < nslots; i += blockDim.x) st.order[i] = kEmptySlot;
+  __syncthreads();
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
     const int r = st.rank[q], b = st.res[q];
-    int pos = 0;
+    int pos = st.rstart[r];
 #pragma unroll
-    for (int g = 0; g < NRES; ++g) pos += min(sz[g], r) + ((g < b && sz[g] > r) ? 1 : 0);
+    for (int g = 0; g < NRES; ++g) pos += (g < b && sz[g] > r) ? 1 : 0;
     st.order[pos] = (unsigned short)q;
   }
   __syncthreads();
+  return nslots;
 }
 
 // Per-point kernel values along one dimension.
@@ -389,7 +448,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
   using I = typename F::I;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_SPREAD];
-  __shared__ int s_sub, s_bin;
+  __shared__ int s_sub, s_bin, s_nslots;
   __shared__ long long s_goff;
   __shared__ Geom s_geo;
   __shared__ I s_maxbits;
@@ -449,7 +508,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
     else
       atomicMax(reinterpret_cast<unsigned long long*>(&s_maxbits),
                 (unsigned long long)__double_as_longlong((double)mloc));
-    bucket_order<T, D, NRES_SPREAD>(cnt, st, hist);
+    const int nslots = bucket_order<T, D, NRES_SPREAD, false>(cnt, st, hist, &s_nslots);
 
     T maxabs;
     if (sizeof(T) == 4)
@@ -465,8 +524,9 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
       inv = T(NAN);  // non-finite strengths: make the whole tile NaN
     }
 
-    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const int q = st.order[sl];
+      if (q == kEmptySlot) continue;
       const Rec rq = rec[p0 + q];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
@@ -527,7 +587,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, con
   using Rec = typename Traits<T>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_INTERP];
-  __shared__ int s_sub, s_bin;
+  __shared__ int s_sub, s_bin, s_nslots;
   __shared__ long long s_goff;
   __shared__ Geom s_geo;
 
@@ -575,10 +635,11 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, con
       }
     }
     cp_async_wait_all();
-    bucket_order<T, D, NRES_INTERP>(cnt, st, hist);
+    const int nslots = bucket_order<T, D, NRES_INTERP, true>(cnt, st, hist, &s_nslots);
 
-    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const int q = st.order[sl];
+      if (q == kEmptySlot) continue;
       const Rec rq = rec[p0 + q];
       T k0[W];
       int ts0, ts1 = 0, ts2 = 0;
@@ -661,7 +722,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
   using Rec = typename Traits<double>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_INTERP];
-  __shared__ int s_sub, s_bin, s_maxexp;
+  __shared__ int s_sub, s_bin, s_maxexp, s_nslots;
   __shared__ long long s_goff;
   __shared__ Geom s_geo;
 
@@ -716,10 +777,11 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
       const DF re = df_of(ldexp(v.x, -sh)), im = df_of(ldexp(v.y, -sh));
       tdf[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
-    bucket_order<double, D, NRES_INTERP>(cnt, st, hist);  // synchronises
+    const int nslots = bucket_order<double, D, NRES_INTERP, true>(cnt, st, hist, &s_nslots);  // synchronises
 
-    for (int sl = threadIdx.x; sl < cnt; sl += blockDim.x) {
+    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const int q = st.order[sl];
+      if (q == kEmptySlot) continue;
       const Rec rq = rec[p0 + q];
       DF k0[W];
       int ts0, ts1 = 0, ts2 = 0;
@@ -1018,7 +1080,7 @@ template <typename T, int D>
 inline size_t spread_bytes(const Geom& g) {
   using I = typename Fixed<T>::I;
   return 2 * (size_t)g.ntile * sizeof(I) + (size_t)g.maxsub * sizeof(typename Traits<T>::C) +
-         stage_bytes<T, D>(g.maxsub);
+         stage_bytes<T, D>(g.maxsub, false);
 }
 template <typename T, int D>
 inline size_t interp_bytes(const Geom& g) {
