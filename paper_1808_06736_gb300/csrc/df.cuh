@@ -18,6 +18,33 @@ __device__ __forceinline__ DF df_of(double x) {
 }
 __device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
 
+// ilogb(|x|) + 1 of a normal double from its exponent field; -1100 for zero, subnormals,
+// infinities and NaN, which take no part in a tile's scale
+__device__ __forceinline__ int df_bexp(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return (e == 0 || e == 0x7ff) ? -1100 : e - 1022;
+}
+
+// x 2^-sh as a pair of floats using integer and FP32 operations only: hi the leading 24
+// bits of the 53-bit significand (truncated, exact), lo the remaining 29 bits rounded to a
+// float, so hi + lo = x 2^-sh to a relative 2^-47.  Zero and subnormal x give 0 (below any
+// float once the tile's largest value is scaled to [0.5, 1)); infinities and NaN give NaN.
+__device__ __forceinline__ DF df_split_scaled(double x, int sh) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return DF{0.0f, 0.0f};
+  if (e == 0x7ff) return DF{__int_as_float(0x7fc00000), 0.0f};
+  const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffULL) | (1ULL << 52);
+  const int E = e - 1023 - sh;  // x 2^-sh = +-m 2^(E - 52)
+  float hi = ldexpf(__uint2float_rn((unsigned)(m >> 29)), E - 23);
+  float lo = ldexpf(__uint2float_rn((unsigned)(m & ((1u << 29) - 1))), E - 52);
+  if (b < 0) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return DF{hi, lo};
+}
+
 // FastTwoSum: |a| >= |b|
 __device__ __forceinline__ DF df_quick(float a, float b) {
   const float s = __fadd_rn(a, b);

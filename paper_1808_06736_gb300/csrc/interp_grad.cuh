@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256, MinBlocksGrad<T>::value) k_interp_grad(Ge
     cp_async_commit();
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) stage_point<T, D, W, NRES_INTERP>(g, rec[p0 + q], q, st, hist);
     cp_async_wait_all();
-    const int nslots = bucket_order<T, D, NRES_INTERP, true>(cnt, st, hist, &s_nslots);
+    const int nslots = bucket_order<T, D, NRES_INTERP, false>(cnt, st, hist, &s_nslots);
 
     for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const int q = st.order[sl];

@@ -284,8 +284,9 @@ __device__ __forceinline__ void stage_point(const Geom& g, const typename Traits
 //    one round, which gapless packing does at the tail of uneven groups.  Each gap is
 //    smaller than the round that did not fit, so there are fewer than 2 cnt slots.
 //    Returns the number of slots.
-// The interpolation kernels take the aligned order (1.6-2.8 % faster on the 3D benchmark
-// workload); the spread keeps the gapless one (its aligned variant measured 11 % slower).
+// The complex64 interpolation takes the aligned order (1.6-2.8 % faster on the 3D benchmark
+// workload); the spread (11 % slower aligned), the double-float interpolation (7 % slower)
+// and the gradient kernels keep the gapless one.
 // Synchronises the block.
 template <typename T, int D, int NRES, bool ALIGNED>
 __device__ __forceinline__ int bucket_order(int cnt, Stage<T, D>& st, const int* hist, int* s_nslots) {
@@ -762,22 +763,25 @@ __global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_const
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) stage_point<double, D, W, NRES_INTERP>(g, rec[p0 + q], q, st, hist);
     cp_async_wait_all();
     __syncthreads();
-    // power-of-two scale: the largest |value| of the tile to [0.5, 1)
+    // power-of-two scale: the largest |value| of the tile to [0.5, 1); exponents read from
+    // the bit patterns (integer pipe), as is the split below, so the GB300's slow FP64
+    // pipe does no per-cell work
     int me = -1100;
     for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
       const double2 v = tile[t];
-      const double m = fmax(fabs(v.x), fabs(v.y));
-      if (m > 0.0) me = max(me, ilogb(m) + 1);
+      me = max(me, max(df_bexp(v.x), df_bexp(v.y)));
     }
     atomicMax(&s_maxexp, me);
     __syncthreads();
     const int sh = s_maxexp > -1000 ? s_maxexp : 0;
     for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
       const double2 v = tile[t];
-      const DF re = df_of(ldexp(v.x, -sh)), im = df_of(ldexp(v.y, -sh));
+      const DF re = df_split_scaled(v.x, sh), im = df_split_scaled(v.y, sh);
       tdf[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
-    const int nslots = bucket_order<double, D, NRES_INTERP, true>(cnt, st, hist, &s_nslots);  // synchronises
+    // gapless order: this kernel is bound by its double-float arithmetic, and the aligned
+    // order's extra (partly idle) warps cost more than its fewer bank conflicts save
+    const int nslots = bucket_order<double, D, NRES_INTERP, false>(cnt, st, hist, &s_nslots);  // synchronises
 
     for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const int q = st.order[sl];
