@@ -525,7 +525,17 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
       inv = T(NAN);  // non-finite strengths: make the whole tile NaN
     }
 
-    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
+    // complex128 in 3D: a subproblem of few points (about a hundred per 8x8x8 bin at
+    // w = 10) would leave most threads idle through the heavy part, w^3 cells per point, so
+    // up to 8 threads share a point, each taking every tpp-th plane of its stencil
+    constexpr bool kSplit = sizeof(T) == 8 && D == 3;
+    int tpp = 1;
+    if constexpr (kSplit) {
+      while (tpp < 8 && tpp < W && 2 * tpp * cnt <= (int)blockDim.x) tpp *= 2;
+    }
+    const int ltpp = kSplit ? __ffs(tpp) - 1 : 0;
+    for (int u = threadIdx.x; u < (nslots << ltpp); u += blockDim.x) {
+      const int sl = u >> ltpp, part = u & (tpp - 1);
       const int q = st.order[sl];
       if (q == kEmptySlot) continue;
       const Rec rq = rec[p0 + q];
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
       constexpr int W1 = (D > 1) ? W : 1;
       constexpr int W2 = (D > 2) ? W : 1;
 #pragma unroll 1
-      for (int l2 = 0; l2 < W2; ++l2) {
+      for (int l2 = part; l2 < W2; l2 += tpp) {
         T k2 = T(1);
         if constexpr (D > 2) k2 = kernel_node<T, W>(ke, l2, st2, f2);
         const T cr2 = cr * k2, ci2 = ci * k2;
