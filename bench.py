@@ -127,7 +127,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # raw samples go to a scratch file; the summary is part of the JSON line
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "nufft_bench_clocks_rank%d_%d.csv" % (index, os.getpid()))
 
     def start(self):
         try:
