@@ -90,6 +90,25 @@ def test_make_plan_validates_before_device_use(lib):
     assert lib.nufft_destroy(None) == 0
 
 
+def test_type3_and_peaks_validate_before_device_use(lib):
+    # type 3: dimension, sign, tolerance and precision are checked before any device call
+    assert lib.nufft3_makeplan(0, 1, 1e-6, 1, None, None)[0] == -1
+    assert lib.nufft3_makeplan(4, 1, 1e-6, 1, None, None)[0] == -1
+    assert lib.nufft3_makeplan(2, 0, 1e-6, 1, None, None)[0] == -1
+    assert lib.nufft3_makeplan(2, 1, -1.0, 1, None, None)[0] == -1
+    assert lib.nufft3_makeplan(2, 1, 1e-6, 7, None, None)[0] == -1
+    assert lib.nufft3_setpts(None, 10, 0, 0, 0, 10, 0, 0, 0) == -1
+    assert lib.nufft3_execute(None, 0, 0) == -1
+    assert lib.nufft3_plan_info(None, 2)[0] == -1
+    assert lib.nufft3_get_status(None) == -1
+    assert lib.nufft3_destroy(None) == 0
+    # the peak microbenchmarks need room for four figures
+    import ctypes
+    assert lib._L().nufft_measure_peaks(None, None, 4) == -1
+    buf = (ctypes.c_double * 2)()
+    assert lib._L().nufft_measure_peaks(None, buf, 2) == -1
+
+
 def test_tune_candidates_host_only(lib):
     for d, default in ((1, (1024, 1, 1)), (2, (32, 32, 1)), (3, (16, 8, 8))):
         for prec in (lib.NUFFT_C64, lib.NUFFT_C128):
