@@ -435,3 +435,41 @@ def test_parity_cosh_kernel(pkg, oracle_mod, cdtype, eps, d):
     h2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype, kernel=1, kerevalmeth=1)
     assert oracle_mod.rel_l2(h1[0], o1_1) <= 10 * eps
     assert oracle_mod.rel_l2(h2[0], o1_2) <= 10 * eps
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex128, 1e-10)])
+def test_all_points_in_one_place(pkg, oracle_mod, cdtype, eps):
+    """Degenerate clustering: 200 000 points on one location (one bin far above the crowded-bin
+    threshold, every point in one bank group) and 200 000 points inside a single bin.  Type 1 of
+    the coincident points is (sum_j c_j) exp(i k.x0) (Eq. (1)); type 2 gives one value at all of
+    them; the single-bin cloud is checked against the exact sums on sampled modes."""
+    import torch
+    dev = torch.device("cuda:0")
+    tdt = torch.complex64 if cdtype == np.complex64 else torch.complex128
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    Ns = [24, 20, 16]
+    M = 200_000
+    x0 = [0.9, -2.2, 1.4]
+    xs = [np.full(M, v, dtype=rdt) for v in x0]
+    c = I.complex_normal(8, M, dtype=cdtype)
+    g1, _ = gpu_transform(pkg, 1, Ns, xs, c, eps, 1, cdtype)
+    k3, k2, k1 = np.meshgrid(*[np.arange(n) - n // 2 for n in reversed(Ns)], indexing="ij")
+    x064 = [float(np.asarray(v, dtype=rdt)) for v in x0]
+    ref = c.astype(np.complex128).sum() * np.exp(1j * (k1 * x064[0] + k2 * x064[1] + k3 * x064[2])).ravel()
+    assert oracle_mod.rel_l2(g1[0], ref) <= 10 * eps
+    f = I.complex_normal(9, int(np.prod(Ns)), dtype=cdtype)
+    g2, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, -1, cdtype)
+    one = oracle_mod.direct_type2([np.array([v]) for v in x064], f.astype(np.complex128), -1, Ns)[0]
+    # each output is one sum of N terms of random phase, of size ~ ||f||_2
+    assert np.max(np.abs(g2[0] - one)) <= 10 * eps * max(abs(one), np.linalg.norm(f.astype(np.complex128)))
+    # a cloud inside one fine-grid bin (a few cells wide)
+    w, beta, ns = oracle_mod.choose_params(eps, Ns)
+    h = 2 * np.pi / np.array(ns)
+    rng = np.random.default_rng(10)
+    cloud = [np.asarray(x0[i] + rng.uniform(0, 3 * h[i], M), dtype=rdt) for i in range(3)]
+    g3, _ = gpu_transform(pkg, 1, Ns, cloud, c, eps, 1, cdtype)
+    modes = oracle_mod.mode_list(Ns)
+    pick = rng.choice(modes.shape[0], 40, replace=False)
+    ref3 = oracle_mod.direct_type1([v.astype(np.float64) for v in cloud], c, 1, Ns, modes=modes[pick])
+    got3 = g3[0][oracle_mod.mode_index(modes[pick], Ns)]
+    assert oracle_mod.rel_l2(got3, ref3) <= 10 * eps
