@@ -103,6 +103,13 @@ struct KEval {
   T a[W * NC];
 };
 
+// The ES kernel for the complex128 kernels, evaluated in double-float (df.cuh: square root by a
+// Newton step, exponential by Cody-Waite reduction and a degree-13 Taylor series, ~2^-47
+// relative) and returned as a double.  The GB300's FP64 pipe, about 1/64 of FP32, would
+// otherwise spend some 40 operations on each kernel value's exp and sqrt, as much FP64 work as
+// a point's w^3 fixed-point products take in the complex128 spread.
+__device__ __forceinline__ double es_eval_dd(double z, double beta) { return df_to(es_eval_df(z, df_of(beta))); }
+
 // Node t of a coordinate with fraction f and stencil step lies at
 // tau = t - floor(w/2) + step - f cells, in the unit interval t of the support
 // [-w/2, w/2]; its local variable is s = 2 (tau - t + w/2) - 1.
@@ -123,7 +130,10 @@ __device__ __forceinline__ T kernel_node(const KEval<T, W>& ke, int t, int step,
     for (int m = NC - 2; m >= 0; --m) y = fma(y, x, a[m]);
     return y;
   }
-  return es_eval(node_z<W>(t, step, f), ke.kpar);
+  if constexpr (sizeof(T) == 8)  // the ES formula in double-float on the FP32 pipe (see es_eval_dd)
+    return es_eval_dd(node_z<W>(t, step, f), ke.kpar);
+  else
+    return es_eval(node_z<W>(t, step, f), ke.kpar);
 }
 
 // kernel values of all W nodes of a coordinate
@@ -138,6 +148,9 @@ __device__ __forceinline__ void kernel_row(const KEval<T, W>& ke, int step, T f,
     for (int m = NC - 2; m >= 0; --m)
 #pragma unroll
       for (int t = 0; t < W; ++t) k[t] = fma(k[t], x, ke.a[t * NC + m]);
+  } else if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int t = 0; t < W; ++t) k[t] = es_eval_dd(node_z<W>(t, step, f), ke.kpar);
   } else {
 #pragma unroll
     for (int t = 0; t < W; ++t) k[t] = es_eval(node_z<W>(t, step, f), ke.kpar);
