@@ -541,3 +541,58 @@ def test_o2_cosh_error_vs_truth(oracle_mod, d, Ns, M, eps):
     assert oracle_mod.rel_l2(t1, oracle_mod.direct_type1(xs, c, 1, Ns)) <= 10 * eps
     assert oracle_mod.rel_l2(t2, oracle_mod.direct_type2(xs, f, -1, Ns)) <= 10 * eps
     assert oracle_mod.rel_l2(t1, oracle_mod.type1(xs, c, 1, Ns, eps=eps)) <= 3 * eps
+
+
+# ------------------------------------------------ aliasing error (Eq. (gkx), (epsest), (1nrm))
+def _single_point_error(oracle_mod, N, n, w, beta, x):
+    """g_k(x) of Eq. (gkx) for k in I_N, written as the finite sum it equals by Poisson summation:
+    (h / psi^(k)) sum_l psi(l h - x) e^{i k l h} - e^{i k x}, psi(t) = phi(t / alpha), alpha = w h / 2,
+    over the grid nodes l h within the kernel's support (numpy; independent of O2's C spreader)."""
+    h = 2 * np.pi / n
+    alpha = w * h / 2
+    k = oracle_mod.mode_range(N)
+    lo, hi = int(np.floor((x - alpha) / h)) - 1, int(np.ceil((x + alpha) / h)) + 1
+    ls = np.arange(lo, hi + 1)
+    psi = oracle_mod.es_kernel((ls * h - x) / alpha, beta)
+    psihat = alpha * oracle_mod.kernel_ft(alpha * k, w, beta)
+    s = (np.exp(1j * np.outer(k, ls * h)) * psi).sum(axis=1)
+    return h / psihat * s - np.exp(1j * k * x)
+
+
+def test_single_point_error_is_the_aliasing_sum(oracle_mod):
+    """Sec. 4.1: for one point (c = 1) the type-1 error is g_k(x), Eq. (gkx); O2 (C spreading,
+    scipy DFT, Eq. (pk1) correction) matches the finite-sum form of g_k to rounding, at points
+    off, on and between grid nodes."""
+    N, eps = 48, 1e-6
+    w, beta, ns = oracle_mod.choose_params(eps, [N])
+    n = ns[0]
+    for x in (0.3, -2.1, 2 * np.pi / n * 5, 2 * np.pi / n * 5.5, np.pi - 1e-3):
+        f2 = oracle_mod.type1([np.array([x])], np.array([1.0 + 0j]), 1, [N], w=w, beta=beta, ns=ns)
+        g = _single_point_error(oracle_mod, N, n, w, beta, x)
+        np.testing.assert_allclose(f2 - np.exp(1j * oracle_mod.mode_range(N) * x), g, rtol=0, atol=1e-13)
+        assert np.abs(g).max() < 10 * eps
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_l1_linf_bound(oracle_mod, eps):
+    """Eq. (1nrm): max_k |f~_k - f_k| <= eps_inf ||c||_1 and max_j |c~_j - c_j| <= eps_inf ||f||_1, with
+    eps_inf of Eq. (epsest) = max over k and x of |g_k(x)| (g_k is h-periodic in x up to a phase, so
+    x is sampled over one grid cell, 400 points, and the bound is taken 5 % above the sampled max);
+    also eps_inf is within a factor 4 of the heuristic of Remark r:heur."""
+    N = 64
+    w, beta, ns = oracle_mod.choose_params(eps, [N])
+    n = ns[0]
+    h = 2 * np.pi / n
+    eps_inf = max(np.abs(_single_point_error(oracle_mod, N, n, w, beta, x)).max()
+                  for x in np.linspace(0, h, 400, endpoint=False))
+    bound = 1.05 * eps_inf
+    xs = I.points(50, 3000, 1)
+    c = I.complex_normal(51, 3000)
+    f = I.complex_normal(52, N)
+    e1 = np.abs(oracle_mod.type1(xs, c, 1, [N], w=w, beta=beta, ns=ns) - oracle_mod.direct_type1(xs, c, 1, [N])).max()
+    e2 = np.abs(oracle_mod.type2(xs, f, -1, [N], w=w, beta=beta, ns=ns) - oracle_mod.direct_type2(xs, f, -1, [N])).max()
+    assert e1 <= bound * np.abs(c).sum()
+    assert e2 <= bound * np.abs(f).sum()
+    a = math.pi * w / n
+    heur = abs(oracle_mod.kernel_ft([a * (n - N / 2)], w, beta)[0] / oracle_mod.kernel_ft([a * N / 2], w, beta)[0])
+    assert heur / 4 < eps_inf < 4 * heur, (eps_inf, heur)
