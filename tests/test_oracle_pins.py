@@ -260,6 +260,22 @@ def test_o2_single_point(oracle_mod):
         assert np.max(np.abs(f - ref)) < 1e-8
 
 
+def test_o2_single_mode(oracle_mod):
+    """f = delta_{k,k0}: Eq. (2) gives c_j = exp(i isign k0.x_j) at every point (O1 exactly, O2 to eps),
+    for a mode at the Nyquist edge -N/2 and an interior one, both signs."""
+    Ns = [10, 7]
+    xs = I.points(60, 200, 2)
+    modes = oracle_mod.mode_list(Ns)
+    for k0 in ([-5, 3], [2, -1]):
+        f = np.zeros(int(np.prod(Ns)), dtype=np.complex128)
+        f[oracle_mod.mode_index(np.array([k0]), Ns)[0]] = 1.0
+        assert np.array_equal(modes[oracle_mod.mode_index(np.array([k0]), Ns)[0]], k0)
+        for isign in (1, -1):
+            ref = np.exp(1j * isign * (k0[0] * xs[0] + k0[1] * xs[1]))
+            np.testing.assert_allclose(oracle_mod.direct_type2(xs, f, isign, Ns), ref, rtol=0, atol=1e-13)
+            assert np.max(np.abs(oracle_mod.type2(xs, f, isign, Ns, eps=1e-9) - ref)) < 1e-8
+
+
 @pytest.mark.parametrize("d", [1, 2, 3])
 @pytest.mark.parametrize("eps", [1e-4, 1e-10])
 def test_o2_brute_force_tiny_with_edge_points(oracle_mod, d, eps):
