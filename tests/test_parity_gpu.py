@@ -473,3 +473,21 @@ def test_all_points_in_one_place(pkg, oracle_mod, cdtype, eps):
     ref3 = oracle_mod.direct_type1([v.astype(np.float64) for v in cloud], c, 1, Ns, modes=modes[pick])
     got3 = g3[0][oracle_mod.mode_index(modes[pick], Ns)]
     assert oracle_mod.rel_l2(got3, ref3) <= 10 * eps
+
+
+@pytest.mark.parametrize("cdtype,eps", [(np.complex64, 1e-5), (np.complex128, 1e-12)])
+def test_single_mode_closed_form(pkg, oracle_mod, cdtype, eps):
+    """f = delta_{k,k0} (the Nyquist corner -N/2 in every dimension, and an interior mode):
+    Eq. (2) gives c_j = exp(i isign k0.x_j) at every point."""
+    Ns = [12, 10, 8]
+    M = 5000
+    rdt = np.float32 if cdtype == np.complex64 else np.float64
+    xs = I.points(61, M, 3, dtype=rdt)
+    x64 = [v.astype(np.float64) for v in xs]
+    for k0 in ([-6, -5, -4], [3, -2, 1]):
+        f = np.zeros(int(np.prod(Ns)), dtype=cdtype)
+        f[oracle_mod.mode_index(np.array([k0]), Ns)[0]] = 1.0
+        for isign in (1, -1):
+            g, _ = gpu_transform(pkg, 2, Ns, xs, f, eps, isign, cdtype)
+            ref = np.exp(1j * isign * sum(k0[i] * x64[i] for i in range(3)))
+            assert oracle_mod.rel_l2(g[0], ref) <= 10 * eps
