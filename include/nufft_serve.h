@@ -20,14 +20,18 @@
  *    stresses this footprint (RAM column of its Table t:big).  Idle entries
  *    are destroyed, least recently used first, when a new one would not fit.
  *  - The host never blocks on the device: completions arrive through host
- *    callbacks on the slot streams; a request that is not done within the
- *    time limit is reported with NUFFT_ERR_TIMEOUT (its entry stays out of
- *    use until its work does finish).
+ *    callbacks on the slot streams.  A request that is not done within the
+ *    time limit is reported early with NUFFT_ERR_TIMEOUT and pending = 1: its
+ *    kernels may still be running and writing its outputs.  Its entry and
+ *    slot stay out of use until the work ends, and then a second, final
+ *    completion for the same ticket (pending = 0, status of the work) follows.
  *
  * Threading: one scheduler thread per server; submit / poll / drain /
  * stats may be called from any host thread.  All pointers in a request are
  * device memory on the server's device, owned by the caller, and must stay
- * valid (inputs unchanged) until the request's completion has been polled.
+ * valid (inputs unchanged) until the request's FINAL completion (pending = 0)
+ * has been polled, or until nufft_server_drain has returned NUFFT_OK.  A
+ * pending TIMEOUT completion does not release them.
  */
 #ifndef NUFFT_SERVE_H
 #define NUFFT_SERVE_H
@@ -79,8 +83,11 @@ typedef struct {
   double t_submit; /* seconds on nufft_server_clock() */
   double t_admit;  /* slot and memory granted, work enqueued */
   double t_done;   /* the device finished (or the time limit expired) */
+  int pending;     /* 1: an early NUFFT_ERR_TIMEOUT report; the request's device work has not ended and a
+                      final completion with the same ticket follows.  0: final; the request's buffers are free */
 } nufft_completion;
 
+/* completed counts final completions; timeouts counts early NUFFT_ERR_TIMEOUT reports */
 typedef struct {
   int64_t submitted, completed, timeouts, rejected;
   int64_t entries_created, entries_evicted, entries_reused, binning_skipped;
@@ -111,7 +118,9 @@ int nufft_server_drain(nufft_server s, double timeout_s);
 int nufft_server_stats_get(nufft_server s, nufft_server_stats* st);
 
 /* Stop the scheduler, fail queued requests with NUFFT_ERR_SHUTDOWN, wait for
- * running work, free every plan entry.  NULL is accepted. */
+ * running work (up to 60 s), free every plan entry.  Entries whose work the
+ * executor has not reported by then are left allocated (leaked), not freed
+ * under running kernels.  NULL is accepted. */
 int nufft_server_destroy(nufft_server s);
 
 /* Seconds on the clock the completions use (a monotonic clock). */
@@ -147,6 +156,9 @@ typedef struct {
 int nufft_server_create_with_executor(const nufft_executor* ex, size_t budget_bytes, int max_inflight,
                                       double timeout_s, nufft_server* out);
 void nufft_server_complete(nufft_server s, int64_t ticket, int status);
+/* How long nufft_server_destroy waits for running work before it leaks the
+ * entries of requests the executor has not reported (default 60 s; > 0). */
+int nufft_server_set_shutdown_wait(nufft_server s, double seconds);
 
 #ifdef __cplusplus
 }

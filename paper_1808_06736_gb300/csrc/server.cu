@@ -325,6 +325,7 @@ struct nufft_server_s {
   size_t budget = 0;
   int max_inflight = 1;
   double timeout = 0;
+  double shutdown_wait = 60.0;  // destroy: how long to wait for running work
 
   struct Entry {
     void* h = nullptr;
@@ -371,7 +372,7 @@ struct nufft_server_s {
   uint64_t use_clock = 0;
   std::thread worker;
 
-  void report(std::vector<nufft_completion>& out, Req* q, int status, double t) {
+  void report(std::vector<nufft_completion>& out, Req* q, int status, double t, int pending = 0) {
     nufft_completion c;
     c.ticket = q->ticket;
     c.tag = q->r.tag;
@@ -380,6 +381,7 @@ struct nufft_server_s {
     c.t_submit = q->t_submit;
     c.t_admit = q->t_admit;
     c.t_done = t;
+    c.pending = pending;
     out.push_back(c);
   }
 
@@ -388,8 +390,8 @@ struct nufft_server_s {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& c : out) {
       done.push_back(c);
-      st.completed++;
-      if (c.status == NUFFT_ERR_TIMEOUT) st.timeouts++;
+      if (c.pending) st.timeouts++;
+      else st.completed++;
       if (c.status == NUFFT_ERR_REJECTED) st.rejected++;
     }
     out.clear();
@@ -506,8 +508,9 @@ struct nufft_server_s {
     return 1;
   }
 
+  // the request's work has ended: its final completion (a second one after an early time-limit report)
   void retire(Req* q, std::vector<nufft_completion>& out, int status, double t) {
-    if (!q->reported) report(out, q, status, t);
+    report(out, q, status, t);
     release(q);
     inflight.erase(q->ticket);
     delete q;
@@ -539,7 +542,7 @@ struct nufft_server_s {
         for (auto& kv : inflight) {
           Req* q = kv.second;
           if (!q->reported && t >= q->t_admit + timeout) {
-            report(out, q, NUFFT_ERR_TIMEOUT, t);
+            report(out, q, NUFFT_ERR_TIMEOUT, t, 1);  // early: the work is still running
             q->reported = true;
           }
         }
@@ -580,7 +583,7 @@ struct nufft_server_s {
     {
       std::lock_guard<std::mutex> lk(mu);
       for (Req* q : queue) {
-        nufft_completion c{q->ticket, q->r.tag, NUFFT_ERR_SHUTDOWN, 0, q->t_submit, 0.0, now_s()};
+        nufft_completion c{q->ticket, q->r.tag, NUFFT_ERR_SHUTDOWN, 0, q->t_submit, 0.0, now_s(), 0};
         done.push_back(c);
         st.completed++;
         delete q;
@@ -590,7 +593,12 @@ struct nufft_server_s {
     }
     if (gpu)
       for (cudaStream_t s : gpu->streams) cudaStreamSynchronize(s);
-    const double give_up = now_s() + 60.0;
+    double wait_s;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      wait_s = shutdown_wait;
+    }
+    const double give_up = now_s() + wait_s;
     while (!inflight.empty() && now_s() < give_up) {
       std::vector<Fin> fin;
       {
@@ -604,9 +612,20 @@ struct nufft_server_s {
       }
       publish(out);
     }
-    for (auto& kv : inflight) delete kv.second;  // executor never reported: leak their entries' state
+    // the executor never reported these requests: their entries may still be in use on the device, so
+    // they are leaked (not destroyed); the requests themselves get no final completion
+    for (auto& kv : inflight) delete kv.second;
     inflight.clear();
-    while (!entries.empty()) destroy_entry(entries.size() - 1);
+    while (!entries.empty()) {
+      Entry* e = entries.back();
+      if (e->busy) {
+        used -= e->bytes;
+        entries.pop_back();
+        delete e;
+      } else {
+        destroy_entry(entries.size() - 1);
+      }
+    }
     publish(out);
   }
 };
@@ -719,6 +738,13 @@ int nufft_server_submit(nufft_server s, const nufft_request* r, int64_t* ticket)
   s->st.queued = (int64_t)s->queue.size();
   s->events++;
   s->cv_worker.notify_one();
+  return NUFFT_OK;
+}
+
+int nufft_server_set_shutdown_wait(nufft_server s, double seconds) {
+  if (!s || !(seconds > 0)) return NUFFT_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->shutdown_wait = seconds;
   return NUFFT_OK;
 }
 

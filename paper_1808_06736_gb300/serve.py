@@ -36,7 +36,7 @@ class nufft_request(ctypes.Structure):
 class nufft_completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_int64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
                 ("reused", ctypes.c_int), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("pending", ctypes.c_int)]
 
 
 class nufft_server_stats(ctypes.Structure):
@@ -73,6 +73,7 @@ def _L():
         lib.nufft_server_submit.argtypes = [vp, ctypes.POINTER(nufft_request), ctypes.POINTER(i64)]
         lib.nufft_server_poll.argtypes = [vp, ctypes.POINTER(nufft_completion), i32, ctypes.POINTER(i32), dbl]
         lib.nufft_server_drain.argtypes = [vp, dbl]
+        lib.nufft_server_set_shutdown_wait.argtypes = [vp, dbl]
         lib.nufft_server_stats_get.argtypes = [vp, ctypes.POINTER(nufft_server_stats)]
         lib.nufft_server_destroy.argtypes = [vp]
         lib.nufft_server_clock.argtypes = []
@@ -111,6 +112,10 @@ def nufft_server_poll(server, max_n: int = 256, wait_s: float = 0.0):
     n = ctypes.c_int()
     st = _L().nufft_server_poll(server, buf, int(max_n), ctypes.byref(n), float(wait_s))
     return st, [buf[i] for i in range(n.value)]
+
+
+def nufft_server_set_shutdown_wait(server, seconds: float) -> int:
+    return _L().nufft_server_set_shutdown_wait(server, float(seconds))
 
 
 def nufft_server_drain(server, timeout_s: float = 0.0) -> int:
@@ -175,6 +180,7 @@ class Completion:
     t_admit: float
     t_done: float
     outputs: dict = field(default_factory=dict)
+    pending: int = 0  # 1: an early time-limit report; the final completion of the ticket follows
 
 
 class Server:
@@ -204,7 +210,7 @@ class Server:
         self._h = h
         self.budget_bytes = int(budget_bytes)
         self._live = {}
-        self._late = []
+        self._late = {}  # ticket -> tensors of a request reported early (time limit), held until its final completion
 
     def _coords(self, x, rdt):
         torch = self._torch
@@ -283,9 +289,13 @@ class Server:
         st, cs = nufft_server_poll(self._h, max_n, wait_s)
         out = []
         for c in cs:
-            keep = self._live.pop(c.ticket, (None, {}, None))
-            if c.status == NUFFT_ERR_TIMEOUT:
-                self._late.append(keep)  # its work may still run: hold its tensors until drain()
+            if c.pending:  # its kernels may still write: hold its tensors until the final completion
+                self._late[c.ticket] = self._live.pop(c.ticket, (None, {}, None))
+                out.append(Completion(c.ticket, c.tag, c.status, c.reused, c.t_submit, c.t_admit, c.t_done, {}, 1))
+                continue
+            keep = self._live.pop(c.ticket, None)
+            if keep is None:
+                keep = self._late.pop(c.ticket, (None, {}, None))
             out.append(Completion(c.ticket, c.tag, c.status, c.reused, c.t_submit, c.t_admit, c.t_done,
                                   keep[1] if c.status == 0 else {}))
         return out
@@ -293,7 +303,7 @@ class Server:
     def drain(self, timeout_s: float = 0.0) -> int:
         st = nufft_server_drain(self._h, timeout_s)
         if st == 0:
-            self._late = []
+            self._late = {}
         return st
 
     def stats(self) -> dict:
@@ -308,7 +318,7 @@ class Server:
             nufft_server_destroy(self._h)
         self._h = None
         self._live = {}
-        self._late = []
+        self._late = {}  # ticket -> tensors of a request reported early (time limit), held until its final completion
 
     def __del__(self):
         try:

@@ -238,19 +238,73 @@ def test_time_limit_reports_and_holds_the_slot():
     t2 = f.submit()
     t0 = time.time()
     done = f.poll_all(1, timeout=2.0)
-    assert done[0].ticket == t1 and done[0].status == S.NUFFT_ERR_TIMEOUT
+    # an early report: the work still runs, so the caller's buffers are not yet free
+    assert done[0].ticket == t1 and done[0].status == S.NUFFT_ERR_TIMEOUT and done[0].pending == 1
     assert 0.04 <= time.time() - t0 < 1.5
     time.sleep(0.05)
     assert len(f.launches) == 1  # the slot is still held by the unfinished work
     assert S.nufft_server_drain(f.h, 0.05) == S.NUFFT_ERR_TIMEOUT
-    f.complete(t1)               # the late finish frees it; no second completion for t1
-    assert f.wait_launches(2)
+    assert S.nufft_server_poll(f.h, 8, 0.05)[1] == []  # no final completion while the work runs
+    f.complete(t1)               # the late finish frees it and sends t1's final completion
+    done = f.poll_all(1)
+    assert done[0].ticket == t1 and done[0].status == 0 and done[0].pending == 0
+    assert done[0].t_done >= done[0].t_admit + 0.05  # the final report is the late finish, after the limit
+    assert f.wait_launches(2)    # only then does the slot take the next request
     f.complete(t2)
     done = f.poll_all(1)
-    assert done[0].ticket == t2 and done[0].status == 0
+    assert done[0].ticket == t2 and done[0].status == 0 and done[0].pending == 0
     assert S.nufft_server_poll(f.h, 8, 0.05)[1] == []
-    assert S.nufft_server_stats_get(f.h)["timeouts"] == 1
+    st = S.nufft_server_stats_get(f.h)
+    assert st["timeouts"] == 1 and st["completed"] == 2
     f.close()
+
+
+def test_final_completion_comes_after_the_work_ends():
+    # the executor finishes every request after the time limit: each ticket gets an early
+    # TIMEOUT report first and its final completion only once the executor has reported it
+    f = Fake(budget=10 ** 9, max_inflight=2, timeout_s=0.02)
+    tickets = [f.submit(tag=i) for i in range(4)]
+    finished_at = {}
+    seen = []
+    t_end = time.time() + 10
+    while len(finished_at) < 4 and time.time() < t_end:
+        time.sleep(0.05)  # well past the limit
+        with f.lock:
+            running = list(f.inflight)
+        for t in running:
+            finished_at[t] = S.nufft_server_clock()
+            f.complete(t)
+        seen += S.nufft_server_poll(f.h, 64, 0.0)[1]
+    seen += f.poll_all(8 - len(seen), timeout=2.0)
+    assert sorted(finished_at) == tickets
+    for t in tickets:
+        cs = [c for c in seen if c.ticket == t]
+        assert [c.pending for c in cs] == [1, 0], cs
+        assert cs[0].status == S.NUFFT_ERR_TIMEOUT and cs[1].status == 0
+        assert cs[1].t_done >= finished_at[t] - 0.01  # final only after the executor reported the work done
+    assert not f.errors
+    f.close()
+
+
+def test_shutdown_leaks_entries_the_executor_never_finished():
+    # destroy waits (here 0.2 s) for running work; the entry of a request the executor never
+    # reports may still be in use on the device, so it is not destroyed; idle entries are
+    f = Fake(budget=10 ** 9, max_inflight=2)
+    assert S.nufft_server_set_shutdown_wait(f.h, 0.2) == 0
+    assert S.nufft_server_set_shutdown_wait(f.h, 0.0) == -1
+    ta = f.submit(n=(8, 8), tag=1)
+    tb = f.submit(n=(16, 16), tag=2)
+    assert f.wait_launches(2)
+    f.complete(tb)
+    assert f.poll_all(1)[0].ticket == tb
+    with f.lock:
+        stuck = f.inflight[ta]
+    t0 = time.time()
+    f.close()  # ta never completes
+    assert 0.15 <= time.time() - t0 < 5.0
+    assert not f.errors                     # nothing was destroyed while busy
+    assert stuck not in f.destroyed         # the stuck entry was leaked
+    assert len(f.destroyed) == len(f.created) - 1
 
 
 def test_invalid_requests_are_refused_at_submit():
