@@ -351,7 +351,7 @@ int nufft_measure_peaks(void* stream, double* out, int n);
 
 /* ------------------------------------------------------------ no allocation
  * nufft_spread_noalloc -- the spreading step of a complex64 type-1 transform
- * (fine-grid values b_l of Eq. (bl)) for callers that cannot allocate device
+ * onto the fine grid, for callers that cannot allocate device
  * memory: code running under another owner's memory pool or arena, latency-
  * critical paths that cannot take an allocation's implicit synchronisation,
  * and plugin hosts that forbid allocation.  The paper has no counterpart; it
@@ -372,11 +372,12 @@ int nufft_measure_peaks(void* stream, double* out, int n);
  * array's device address is looked up (cudaGetSymbolAddress) during the
  * first call on each device; make that first call before any stream capture.
  *
- * Returns NUFFT_OK; NUFFT_ERR_BAD_ARG (dim, w outside [2, 16], n_i < 2w,
- * beta <= 0, M < 0, NULL pointer); NUFFT_ERR_TOO_BIG when M points and the
- * bins of this grid need more than the 32 MiB array (16 bytes per point plus
- * about 16 bytes per bin: roughly two million points); NUFFT_ERR_CUDA when a
- * launch fails.
+ * Returns NUFFT_OK; NUFFT_ERR_BAD_ARG (dim, w outside [2, 16], n_i < 2w or
+ * > 2^30, beta <= 0, M < 0, NULL pointer); NUFFT_ERR_TOO_BIG when M >= 2^31 - 1,
+ * when the grid has 2^31 or more cells, or when M points and the bins of this
+ * grid need more than the 32 MiB array (16 bytes per point plus about 16
+ * bytes per bin: roughly two million points); NUFFT_ERR_CUDA when a launch
+ * fails.
  */
 int nufft_spread_noalloc(int dim, const int64_t* n, int w, double beta, int64_t M, const float* x,
                          const float* y, const float* z, const void* c, void* grid, void* stream);

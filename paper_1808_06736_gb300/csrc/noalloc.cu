@@ -75,6 +75,9 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
   if (dim < 1 || dim > 3 || !n || w < 2 || w > 16 || !(beta > 0.0) || M < 0 || !grid)
     return NUFFT_ERR_BAD_ARG;
   if (M > 0 && (!x || !c || (dim > 1 && !y) || (dim > 2 && !z))) return NUFFT_ERR_BAD_ARG;
+  // point indices and bin ids are 32-bit on the device: bound M and the grid before any
+  // size arithmetic (so nothing below can overflow)
+  if (M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_TOO_BIG;
   Geom g;
   g.d = dim;
   g.w = w;
@@ -88,9 +91,12 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
     int64_t v = i < dim ? n[i] : 1;
     if (i < dim && (v < 2 * w || v > (1 << 30))) return NUFFT_ERR_BAD_ARG;
     g.n[i] = (int)v;
+    if (ngrid > (((int64_t)1 << 31) - 1) / v) return NUFFT_ERR_TOO_BIG;  // grid cells >= 2^31
     ngrid *= v;
   }
+  // bin ids (at most one bin per cell) then fit in int, so finish_geom cannot overflow
   pick_bins(g);
+  if (g.nbins <= 0) return NUFFT_ERR_TOO_BIG;
 
   // carve the scratch array; reject sizes that do not fit
   const int64_t subcap = std::min<int64_t>(g.nbins, M) + M / g.maxsub + 1;

@@ -5,10 +5,13 @@ memory pool, latency-critical paths that cannot take an allocation's implicit
 synchronisation, plugin hosts that forbid allocation.  For them the library
 offers a spreading entry point whose scratch space is a fixed static device
 array.  This test calls it through the C ABI twice in a row (different inputs,
-so stale scratch contents would show) and checks each fine grid against the
-plan path (nufft_makeplan / nufft_setpts / nufft_execute, type 1): the grid's
-FFT, truncated and multiplied by the library's correction factors, must give
-the plan's modes within the GPU tests' rounding budget for complex64.
+so stale scratch contents would show) and checks each fine grid two ways:
+against the plan path (nufft_makeplan / nufft_setpts / nufft_execute, type 1):
+the grid's FFT, truncated and multiplied by the library's correction factors,
+must give the plan's modes within the GPU tests' rounding budget for
+complex64; and element by element against the oracle's spreading (Eq. (bl),
+fp64) at the same w, beta and n, within that budget relative to the grid's
+l2 norm.
 
 The file name sorts last so a run that stops at the first failure has run
 every other test before this one.
@@ -55,7 +58,7 @@ def _modes_from_grid(pkg, grid, Ns, ns, w, beta, isign):
 
 
 @pytest.mark.parametrize("d,Ns,M", [(3, [24, 20, 18], 40000), (2, [64, 50], 30000)])
-def test_noalloc_spread_matches_plan_path_twice(pkg, d, Ns, M):
+def test_noalloc_spread_matches_plan_path_twice(pkg, oracle_mod, d, Ns, M):
     import torch
     dev = torch.device("cuda:0")
     eps = 1e-5
@@ -71,6 +74,12 @@ def test_noalloc_spread_matches_plan_path_twice(pkg, d, Ns, M):
         rc = pkg.nufft_spread_noalloc(d, ns, w, beta, M, *ptrs, c.data_ptr(), grid.data_ptr(),
                                       stream.cuda_stream)
         assert rc == 0, pkg.nufft_strerror(rc)
+        # the grid itself against the oracle's fp64 spreading of the same (float) coordinates
+        b_ref = oracle_mod.spread([v.double().cpu().numpy() for v in xs], c.cpu().numpy().astype(np.complex128),
+                                  ns, w, beta).ravel()
+        b_got = grid.cpu().numpy().astype(np.complex128)
+        e_grid = np.linalg.norm(b_got - b_ref) / np.linalg.norm(b_ref)
+        assert e_grid <= TOL_C64, (call, e_grid)
         f_noalloc = _modes_from_grid(pkg, grid, Ns, ns, w, beta, 1)
         plan = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=torch.complex64, device=dev)
         plan.setpts(*xs)
@@ -88,3 +97,8 @@ def test_noalloc_rejects_oversized_and_bad_args(pkg):
     assert pkg.nufft_spread_noalloc(3, ns, 1, beta, 10, 1, 1, 1, 1, 1, 0) == -1
     assert pkg.nufft_spread_noalloc(3, [8, 8, 8], w, beta, 10, 1, 1, 1, 1, 1, 0) == -1
     assert pkg.nufft_spread_noalloc(2, ns[:2], w, beta, 10, 1, 0, 0, 1, 1, 0) == -1
+    # sizes whose arithmetic would overflow 32-bit indices are refused before anything is carved
+    assert pkg.nufft_spread_noalloc(3, ns, w, beta, (1 << 31) - 1, 1, 1, 1, 1, 1, 0) == -7
+    assert pkg.nufft_spread_noalloc(3, ns, w, beta, 1 << 62, 1, 1, 1, 1, 1, 0) == -7
+    assert pkg.nufft_spread_noalloc(3, [1 << 30, 1 << 30, 1 << 30], w, beta, 10, 1, 1, 1, 1, 1, 0) == -7
+    assert pkg.nufft_spread_noalloc(2, [1 << 16, 1 << 15], w, beta, 10, 1, 1, 0, 1, 1, 0) == -7
