@@ -78,13 +78,20 @@ def _L():
         lib.oracle_interp.argtypes = [ctypes.c_int, i64, dp, dp, dp, dp, ip, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_int, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
 
 def num_threads() -> int:
-    """OpenMP threads the direct sums use."""
+    """OpenMP threads the direct sums, spreading and interpolation use."""
     return int(_L().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Use n OpenMP threads from now on; returns the number in effect."""
+    return int(_L().oracle_set_num_threads(int(n)))
 
 
 # ----------------------------------------------------------------- helpers

@@ -207,28 +207,57 @@ static void node_weights(double x, int64_t n, int w, double beta, int kernel, in
  * with the tensor-product kernel of Eq. (ppsi).  b (n_1 x ... x n_d complex,
  * dimension 1 fastest) is overwritten.  A plain loop over points, then over
  * the w^d nodes of each point.
+ *
+ * Threads own slabs of the last dimension's grid index (no atomics): every
+ * thread walks all points in order and adds only the nodes whose last index
+ * lies in its slab.  Each grid value therefore receives its contributions in
+ * point order, exactly as a single thread would add them.
  */
 void oracle_spread(int d, int64_t M, const double* x, const double* y, const double* z,
                    const double* c, const int64_t* n, int w, double beta, int kernel, double* b) {
   int64_t nn[3] = {1, 1, 1}, nt = 1;
   for (int i = 0; i < d; ++i) { nn[i] = n[i]; nt *= n[i]; }
   memset(b, 0, sizeof(double) * 2 * (size_t)nt);
-  int64_t idx[3][32];
-  double ker[3][32];
-  for (int64_t j = 0; j < M; ++j) {
-    int w2 = d >= 2 ? w : 1, w3 = d >= 3 ? w : 1;
-    for (int i = 0; i < 3; ++i) {
-      if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, kernel, idx[i], ker[i]);
-      else { idx[i][0] = 0; ker[i][0] = 1.0; }
+  const int last = d - 1;
+  const int64_t nl = nn[last];
+  const double two_pi = 6.283185307179586476925286766559;
+#pragma omp parallel
+  {
+    int th = 0, nth = 1;
+#ifdef _OPENMP
+    th = omp_get_thread_num();
+    nth = omp_get_num_threads();
+#endif
+    const int64_t lo = nl * th / nth, hi = nl * (th + 1) / nth; /* this thread's slab [lo, hi) */
+    int64_t idx[3][32];
+    double ker[3][32];
+    const int wd[3] = {w, d >= 2 ? w : 1, d >= 3 ? w : 1};
+    for (int64_t j = 0; j < M && lo < hi; ++j) {
+      /* skip points none of whose last-dimension nodes lies in the slab */
+      double u = coord(last, x, y, z)[j] * (double)nl / two_pi;
+      int64_t s0 = (int64_t)ceil(u - 0.5 * (double)w) % nl;
+      if (s0 < 0) s0 += nl;
+      int touches = 0;
+      for (int t = 0; t < w && !touches; ++t) {
+        int64_t li = (s0 + t) % nl;
+        touches = li >= lo && li < hi;
+      }
+      if (!touches) continue;
+      for (int i = 0; i < 3; ++i) {
+        if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, kernel, idx[i], ker[i]);
+        else { idx[i][0] = 0; ker[i][0] = 1.0; }
+      }
+      for (int t3 = 0; t3 < wd[2]; ++t3)
+        for (int t2 = 0; t2 < wd[1]; ++t2)
+          for (int t1 = 0; t1 < w; ++t1) {
+            const int tl = last == 0 ? t1 : (last == 1 ? t2 : t3);
+            if (idx[last][tl] < lo || idx[last][tl] >= hi) continue;
+            double kv = ker[0][t1] * ker[1][t2] * ker[2][t3];
+            int64_t g = idx[0][t1] + nn[0] * (idx[1][t2] + nn[1] * idx[2][t3]);
+            b[2 * g] += c[2 * j] * kv;
+            b[2 * g + 1] += c[2 * j + 1] * kv;
+          }
     }
-    for (int t3 = 0; t3 < w3; ++t3)
-      for (int t2 = 0; t2 < w2; ++t2)
-        for (int t1 = 0; t1 < w; ++t1) {
-          double kv = ker[0][t1] * ker[1][t2] * ker[2][t3];
-          int64_t g = idx[0][t1] + nn[0] * (idx[1][t2] + nn[1] * idx[2][t3]);
-          b[2 * g] += c[2 * j] * kv;
-          b[2 * g + 1] += c[2 * j + 1] * kv;
-        }
   }
 }
 
@@ -242,9 +271,11 @@ void oracle_interp(int d, int64_t M, const double* x, const double* y, const dou
                    const double* b, const int64_t* n, int w, double beta, int kernel, double* c) {
   int64_t nn[3] = {1, 1, 1};
   for (int i = 0; i < d; ++i) nn[i] = n[i];
-  int64_t idx[3][32];
-  double ker[3][32];
+  /* points are independent: threads split them */
+#pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < M; ++j) {
+    int64_t idx[3][32];
+    double ker[3][32];
     int w2 = d >= 2 ? w : 1, w3 = d >= 3 ? w : 1;
     for (int i = 0; i < 3; ++i) {
       if (i < d) node_weights(coord(i, x, y, z)[j], nn[i], w, beta, kernel, idx[i], ker[i]);
@@ -287,11 +318,19 @@ void oracle_type3_direct(int d, int64_t M, const double* x, const double* y, con
   }
 }
 
-/* Number of OpenMP threads the direct sums use (1 without OpenMP). */
+/* Number of OpenMP threads the direct sums, spreading and interpolation use (1 without OpenMP). */
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
 #else
   return 1;
 #endif
+}
+
+/* Set that number (n >= 1); returns the number now in effect. */
+int oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#endif
+  return oracle_num_threads();
 }

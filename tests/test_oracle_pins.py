@@ -612,3 +612,29 @@ def test_l1_linf_bound(oracle_mod, eps):
     a = math.pi * w / n
     heur = abs(oracle_mod.kernel_ft([a * (n - N / 2)], w, beta)[0] / oracle_mod.kernel_ft([a * N / 2], w, beta)[0])
     assert heur / 4 < eps_inf < 4 * heur, (eps_inf, heur)
+
+
+@pytest.mark.parametrize("d,ns", [(1, [40]), (2, [24, 12]), (3, [12, 16, 14])])
+def test_threads_do_not_change_spread_or_interp(oracle_mod, d, ns):
+    # the threaded spreading owns slabs of the last grid index and the threaded interpolation
+    # splits the points; both must give the single-thread results bit for bit, also with more
+    # threads than slabs (empty slabs) and with points whose stencil wraps around the grid
+    rng = np.random.default_rng(77 + d)
+    M = 3000
+    xs = [rng.uniform(-np.pi, np.pi, M) for _ in range(d)]
+    xs[0][:4] = [-np.pi, np.pi - 1e-12, 0.0, 3 * np.pi - 1e-9]
+    c = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    w, beta = 6, 13.8
+    b = (rng.standard_normal(int(np.prod(ns))) + 1j * rng.standard_normal(int(np.prod(ns)))).reshape(
+        tuple(reversed(ns)))
+    n0 = oracle_mod.num_threads()
+    try:
+        res = {}
+        for t in (1, 3, 64):
+            assert oracle_mod.set_num_threads(t) == t
+            res[t] = (oracle_mod.spread(xs, c, ns, w, beta), oracle_mod.interp(xs, b, ns, w, beta))
+    finally:
+        oracle_mod.set_num_threads(n0)
+    for t in (3, 64):
+        assert np.array_equal(res[t][0], res[1][0])
+        assert np.array_equal(res[t][1], res[1][1])
