@@ -429,6 +429,16 @@ void finish_geom(Geom& g) {
   }
   g.nbins = nbins;
   g.ntile = ntile;
+  g.qs0 = g.qt1 = g.qtile = 0;
+  if (g.d == 3 && (g.w & 1) == 0) {
+    int s0 = g.T[0] + 1;
+    while ((s0 & 15) != 8) ++s0;
+    int t1 = g.T[1];
+    while ((t1 & 3) != (g.w & 3)) ++t1;
+    g.qs0 = s0;
+    g.qt1 = t1;
+    g.qtile = s0 * t1 * g.T[2];
+  }
 }
 
 namespace {

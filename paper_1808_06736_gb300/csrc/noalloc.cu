@@ -138,7 +138,7 @@ extern "C" int nufft_spread_noalloc(int dim, const int64_t* n, int w, double bet
   if (M == 0) return NUFFT_OK;
   LaunchCfg cfg;
   if (spread_config(false, g, 256, &cfg) != cudaSuccess) return NUFFT_ERR_CUDA;
-  Sorted so{rec, sub_bin, sub_pt0, sub_cnt, small + 1, small + 3};
+  Sorted so{rec, sub_bin, sub_pt0, sub_cnt, small + 1, small + 3, small};
   if (launch_spread(false, g, beta, so, c, grid, small + 2, cfg, st_) != cudaSuccess) return NUFFT_ERR_CUDA;
   return NUFFT_OK;
 }

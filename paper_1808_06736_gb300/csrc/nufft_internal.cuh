@@ -30,7 +30,24 @@ struct Geom {
   int sparse_max;  // subproblems with at most this many points take the per-warp path (0: none)
   int horner;      // 1: kernel values from the piecewise polynomial of Sec. 5.3 (horner_table)
   int kernel;      // 0: the ES kernel, Eq. (ES); 1: 2 e^-beta cosh(beta sqrt(1 - z^2)) (Remark in Sec. 7)
+  // Bank-grouped tile layout of the 3D kernels for even w (0 when it does not apply): rows of qs0
+  // cells (qs0 = 8 mod 16, at least T[0] + 1: the tile's x-origin is rounded down to an even grid
+  // index), qt1 rows per plane (qt1 = w mod 4, at least T[1]), qtile = qs0 qt1 T[2] cells.  With
+  // these strides the cell of stencil row rho = l1 + w l2 lies rho qs0 cells (mod 32) after the
+  // row start, which the quad spread and paired interpolation orders rely on.
+  int qs0, qt1, qtile;
 };
+// true when the bank-grouped tile layout applies (3D, even w)
+__host__ __device__ __forceinline__ bool quad_layout(const Geom& g) { return g.qs0 > 0; }
+// Dynamic shared memory of the bank-grouped complex64 kernels (each with 128 bytes of slack to
+// align the tile for TMA).  Spread: re and im planes of qtile ints, maxsub staged strengths, the
+// point order (5 maxsub shorts).  Interp: the tile (qtile float2), the point order.
+__host__ __device__ inline size_t spread_q_bytes(const Geom& g) {
+  return 128 + 2 * (size_t)g.qtile * 4 + (size_t)g.maxsub * 8 + (size_t)g.maxsub * 5 * 2;
+}
+__host__ __device__ inline size_t interp_q_bytes(const Geom& g) {
+  return 128 + (size_t)g.qtile * 8 + (size_t)g.maxsub * 5 * 2;
+}
 
 // Bin ids run over super-blocks of sb[0] x sb[1] x sb[2] bins, dimension 1
 // fastest inside a super-block and across super-blocks.  Subproblems are
@@ -139,6 +156,7 @@ struct Sorted {
   const int* sub_cnt;  // [nsub] number of records
   const int* nsub;     // device scalar: tiled subproblems, list entries [0, nsub)
   const int* nsparse;  // device scalar: per-warp subproblems, entries [nsub, nsub + nsparse)
+  int* err = nullptr;  // device error word (NUFFT_ERR_*) a kernel sets when a bounded wait runs out
 };
 
 // --- setpts (binsort.cu) ------------------------------------------------------
@@ -179,7 +197,13 @@ struct LaunchCfg {
   int threads;
   int blocks;   // persistent grid
   size_t smem;  // dynamic shared memory bytes
+  // interpolation only: a tensor map (CUtensorMap, 128 bytes) over the plan's own fine grid as
+  // float pairs, box of one bank-grouped tile; NULL: tiles are fetched with per-cell copies
+  const void* tmap = nullptr;
 };
+// Encode *tmap (a CUtensorMap) for TMA loads of bank-grouped tiles from a complex64 fine grid
+// of g.n cells (this GPU's own memory).  Returns false when the layout or the driver does not allow it.
+bool encode_tile_map(const Geom& g, const void* grid, void* tmap);
 // smem bytes a spread / interp kernel needs for this geometry
 size_t spread_smem_bytes(bool dbl, const Geom& g, int threads);
 size_t interp_smem_bytes(bool dbl, const Geom& g, int threads);

@@ -6,11 +6,13 @@
 // setpts    binning pipeline (binsort.cu)
 // execute   type 1: zero grid, spread, FFT, deconvolve
 //           type 2: pre-correct/pad, FFT, interpolate
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -55,6 +57,7 @@ struct nufft_plan_s {
   int* sub_cnt = nullptr;
   cufftHandle fft = 0;
   bool fft_ok = false;
+  alignas(64) unsigned char tmap[128];  // CUtensorMap over grid for the interpolation's tile loads
   LaunchCfg spread_cfg{0, 0, 0}, interp_cfg{0, 0, 0}, grad_cfg{0, 0, 0};
   cudaEvent_t ev[8];
   bool ev_ok = false;
@@ -278,14 +281,50 @@ cudaError_t dev_alloc(P** ptr, size_t bytes) {
 namespace nufft {
 
 size_t spread_smem_bytes(bool dbl, const Geom& g, int) {
+  if (!dbl && quad_layout(g)) return spread_q_bytes(g);
   size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8;
   // the spread's point order is gapless: res, rank and order of maxsub entries each
   return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc + (size_t)g.maxsub * 3 * 2;
 }
-size_t interp_smem_bytes(bool dbl, const Geom& g, int) {
+// the tile with its halo and the aligned point order of the per-point interpolation kernels
+static size_t interp_plain_bytes(bool dbl, const Geom& g) {
   size_t cc = dbl ? 16 : 8;
-  // res, rank, the slot order (2 maxsub) and the round starts of the aligned point order
   return (size_t)g.ntile * cc + (size_t)g.maxsub * 5 * 2;
+}
+size_t interp_smem_bytes(bool dbl, const Geom& g, int) {
+  if (!dbl && quad_layout(g)) return interp_q_bytes(g);
+  return interp_plain_bytes(dbl, g);
+}
+
+// Tensor map for TMA loads of one bank-grouped tile from a complex64 fine grid, seen as a 3D
+// array of floats (2 n_1, n_2, n_3): box (2 qs0, qt1, T_3), no swizzle, zero fill outside the
+// grid (the kernel uses the TMA only for tiles that need no periodic wrap).
+bool encode_tile_map(const Geom& g, const void* grid, void* tmap) {
+  if (!quad_layout(g) || g.d != 3 || (g.n[0] & 1) || !grid || ((uintptr_t)grid & 15)) return false;
+  if (2 * g.qs0 > 256 || g.qt1 > 256 || g.T[2] > 256) return false;  // TMA box limits
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)f;
+    looked = true;
+  }
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {2 * (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+  const cuuint64_t strides[2] = {8 * (cuuint64_t)g.n[0], 8 * (cuuint64_t)g.n[0] * (cuuint64_t)g.n[1]};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * g.qs0), (cuuint32_t)g.qt1, (cuuint32_t)g.T[2]};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(grid),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 static cudaError_t si_dispatch(bool spread, bool dbl, const Geom& g, double beta, const Sorted& s,
@@ -341,7 +380,7 @@ static cudaError_t grad_dispatch(bool dbl, const Geom& g, double beta, const Sor
 
 static cudaError_t grad_config(bool dbl, const Geom& g, int threads, LaunchCfg* cfg) {
   cfg->threads = threads;
-  cfg->smem = interp_smem_bytes(dbl, g, threads);
+  cfg->smem = interp_plain_bytes(dbl, g);  // the gradient kernels keep the per-point tile layout
   cfg->blocks = 0;
   Sorted s{};
   GradOut go{};
@@ -501,6 +540,10 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
   if (spread_config(p->dbl, g, threads, &p->spread_cfg) != cudaSuccess ||
       interp_config(p->dbl, g, threads, &p->interp_cfg) != cudaSuccess)
     return fail(p, NUFFT_ERR_CUDA);
+  if (!p->dbl && quad_layout(g) && encode_tile_map(g, p->grid, p->tmap)) {
+    p->interp_cfg.tmap = p->tmap;  // tile loads (interpolation)
+    p->spread_cfg.tmap = p->tmap;  // tile reductions (spreading); the same box over the same grid
+  }
 
   // cuFFT: dimensions slowest first
   int nn[3];
@@ -573,7 +616,7 @@ int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f) {
   if (!f || (p->M > 0 && !c)) return NUFFT_ERR_BAD_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
   const Geom& g = p->g;
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3, p->small};
   ModeGeom mg;
   mg.d = p->dim;
   mg.modeord = p->opts.modeord ? 1 : 0;
@@ -624,7 +667,7 @@ int plan_execute_grad(nufft_plan p, void* c, void* dc, const void* f) {
     int threads = p->opts.threads > 0 ? p->opts.threads : 256;
     if (grad_config(p->dbl, g, threads, &p->grad_cfg) != cudaSuccess) return NUFFT_ERR_CUDA;
   }
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3, p->small};
   ModeGeom mg;
   mg.d = p->dim;
   mg.modeord = p->opts.modeord ? 1 : 0;
@@ -969,7 +1012,7 @@ int batch_fail(nufft_batch p, int code) {
 // The execute sequence, enqueued on the plan's stream.
 int batch_enqueue(nufft_batch p, void* c, void* f) {
   const BatchTable bt = table_of(p);
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
+  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3, p->small};
   const int dir = p->isign > 0 ? CUFFT_INVERSE : CUFFT_FORWARD;
   const int modeord = p->opts.modeord ? 1 : 0;
   auto ffts = [&]() -> int {

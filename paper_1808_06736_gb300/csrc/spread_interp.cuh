@@ -26,6 +26,9 @@
 // the tile result does not depend on the order of the atomics.
 #pragma once
 
+#include <cstring>
+#include <type_traits>
+
 #include "df.cuh"
 #include "nufft_internal.cuh"
 
@@ -422,6 +425,54 @@ __device__ __forceinline__ void flush_tile(const Geom& g, const int* org, const 
 }
 
 // ----------------------------------------------------------------- spread
+// Fixed-point scales of one complex64 subproblem.  A single scale set by the largest
+// strength maxabs rounds every contribution to steps of maxabs / K; when most strengths of
+// the subproblem lie below maxabs 2^-10 (one large strength among many small ones), those
+// small ones would lose their share to that rounding.  Such subproblems are spread in two
+// passes: the strengths above maxabs 2^-10 at K / maxabs, the others at K / (their own
+// maximum), each pass flushed on its own.  Counted once per subproblem, after staging;
+// s_nsmall and s_msmall must be zero on entry.  Returns the number of passes (1 or 2) and
+// the threshold and the small strengths' maximum.
+constexpr float kSmallRatio = 1.0f / 1024.0f;
+__device__ __forceinline__ int plan_passes(const float2* sc, int cnt, float maxabs, int* s_nsmall, int* s_msmall,
+                                           float* thr, float* smax) {
+  *thr = maxabs * kSmallRatio;
+  int n = 0;
+  float m = 0.f;
+  if (maxabs > 0.f && maxabs < INFINITY) {
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const float a = fmaxf(fabsf(sc[q].x), fabsf(sc[q].y));
+      if (a <= *thr) {
+        ++n;
+        m = fmaxf(m, a);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0 && n > 0) {
+    atomicAdd(s_nsmall, n);
+    atomicMax(s_msmall, __float_as_int(m));
+  }
+  __syncthreads();
+  *smax = __int_as_float(*s_msmall);
+  return (2 * *s_nsmall > cnt && *smax > 0.f) ? 2 : 1;
+}
+// scale K / top and its inverse for a pass over strengths of largest magnitude top
+__device__ __forceinline__ void pass_scale(double K, float top, float* scale, float* inv) {
+  *scale = 0.f;
+  *inv = 0.f;
+  if (top > 0.f && top < INFINITY) {
+    *scale = float(K / (double)top);
+    *inv = float((double)top / K);
+  } else if (!(top == 0.f)) {
+    *inv = NAN;  // non-finite strengths: make the whole tile NaN
+  }
+}
+
 // float kernels are held to 64 registers so four 256-thread blocks fit an SM
 template <typename T>
 struct MinBlocks {
@@ -462,7 +513,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
   using I = typename F::I;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[NRES_SPREAD];
-  __shared__ int s_sub, s_bin, s_nslots;
+  __shared__ int s_sub, s_bin, s_nslots, s_nsmall, s_msmall;
   __shared__ long long s_goff;
   __shared__ Geom s_geo;
   __shared__ I s_maxbits;
@@ -479,6 +530,8 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
     if (threadIdx.x == 0) {
       next_subproblem(g, s, bt, work, &s_sub, &s_bin, &s_goff, &s_geo);
       s_maxbits = 0;
+      s_nsmall = 0;
+      s_msmall = 0;
     }
     if (threadIdx.x < NRES_SPREAD) hist[threadIdx.x] = 0;
     __syncthreads();
@@ -530,74 +583,90 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
     else
       maxabs = (T)__longlong_as_double((long long)s_maxbits);
     const double K = fmin(F::KMAX, floor(F::IMAX / (double)cnt) - 1.0);
-    T scale = T(0), inv = T(0);
-    if (maxabs > T(0) && maxabs < T(INFINITY)) {
-      scale = T(K / (double)maxabs);
-      inv = T((double)maxabs / K);
-    } else if (!(maxabs == T(0))) {
-      inv = T(NAN);  // non-finite strengths: make the whole tile NaN
-    }
-
-    // complex128 in 3D: a subproblem of few points (about a hundred per 8x8x8 bin at
-    // w = 10) would leave most threads idle through the heavy part, w^3 cells per point, so
-    // up to 8 threads share a point, each taking every tpp-th plane of its stencil
-    constexpr bool kSplit = sizeof(T) == 8 && D == 3;
-    int tpp = 1;
-    if constexpr (kSplit) {
-      while (tpp < 8 && tpp < W && 2 * tpp * cnt <= (int)blockDim.x) tpp *= 2;
-    }
-    const int ltpp = kSplit ? __ffs(tpp) - 1 : 0;
-    for (int u = threadIdx.x; u < (nslots << ltpp); u += blockDim.x) {
-      const int sl = u >> ltpp, part = u & (tpp - 1);
-      const int q = st.order[sl];
-      if (q == kEmptySlot) continue;
-      const Rec rq = rec[p0 + q];
-      T k0[W];
-      int ts0, ts1 = 0, ts2 = 0;
-      point_weights<T, W>(rq.v[0], g.B[0], ke, ts0, k0);
-      T k1[(D > 1) ? W : 1];
-      T f2 = T(0);
-      int st2 = 0;
-      if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], ke, ts1, k1);
-      else k1[0] = T(1);
-      if constexpr (D > 2) {
-        T v2 = rq.v[2];
-        int il2 = min((int)v2, g.B[2] - 1);
-        f2 = v2 - T(il2);
-        st2 = stencil_step<W>(f2);
-        ts2 = il2 + st2;
+    // complex64: one or two passes (plan_passes); complex128's 2^51 steps need no split
+    float thr = 0.f, smax = 0.f;
+    int npass = 1;
+    if constexpr (sizeof(T) == 4)
+      npass = plan_passes(reinterpret_cast<const float2*>(sc), cnt, (float)maxabs, &s_nsmall, &s_msmall, &thr, &smax);
+    for (int pass = 0; pass < npass; ++pass) {
+      if (pass == 1) {  // the small strengths, on a zeroed tile
+        for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+          tre[t] = 0;
+          tim[t] = 0;
+        }
+        __syncthreads();
       }
-      const C cv = sc[q];
-      const T cr = cv.x * scale, ci = cv.y * scale;
-      const int base = ts0 + T0 * ts1 + T01 * ts2;
-      constexpr int W1 = (D > 1) ? W : 1;
-      constexpr int W2 = (D > 2) ? W : 1;
-#pragma unroll 1
-      for (int l2 = part; l2 < W2; l2 += tpp) {
-        T k2 = T(1);
-        if constexpr (D > 2) k2 = kernel_node<T, W>(ke, l2, st2, f2);
-        const T cr2 = cr * k2, ci2 = ci * k2;
-#pragma unroll
-        for (int l1 = 0; l1 < W1; ++l1) {
-          const T cr1 = cr2 * k1[l1], ci1 = ci2 * k1[l1];
-          I* pr = tre + base + l1 * T0 + l2 * T01;
-          I* pi = tim + base + l1 * T0 + l2 * T01;
-#pragma unroll
-          for (int l0 = 0; l0 < W; ++l0) {
-            F::add(pr + l0, F::bits(F::quant_fma(cr1, k0[l0])));
-            F::add(pi + l0, F::bits(F::quant_fma(ci1, k0[l0])));
+      T scale = T(0), inv = T(0);
+      const T top = pass == 0 ? maxabs : T(smax);
+      if (top > T(0) && top < T(INFINITY)) {
+        scale = T(K / (double)top);
+        inv = T((double)top / K);
+      } else if (!(top == T(0))) {
+        inv = T(NAN);  // non-finite strengths: make the whole tile NaN
+      }
+
+      // complex128 in 3D: a subproblem of few points (about a hundred per 8x8x8 bin at
+      // w = 10) would leave most threads idle through the heavy part, w^3 cells per point, so
+      // up to 8 threads share a point, each taking every tpp-th plane of its stencil
+      constexpr bool kSplit = sizeof(T) == 8 && D == 3;
+      int tpp = 1;
+      if constexpr (kSplit) {
+        while (tpp < 8 && tpp < W && 2 * tpp * cnt <= (int)blockDim.x) tpp *= 2;
+      }
+      const int ltpp = kSplit ? __ffs(tpp) - 1 : 0;
+      for (int u = threadIdx.x; u < (nslots << ltpp); u += blockDim.x) {
+        const int sl = u >> ltpp, part = u & (tpp - 1);
+        const int q = st.order[sl];
+        if (q == kEmptySlot) continue;
+        if (npass == 2 && (fmax(fabs(sc[q].x), fabs(sc[q].y)) > T(thr)) != (pass == 0)) continue;  // not this pass
+        const Rec rq = rec[p0 + q];
+        T k0[W];
+        int ts0, ts1 = 0, ts2 = 0;
+        point_weights<T, W>(rq.v[0], g.B[0], ke, ts0, k0);
+        T k1[(D > 1) ? W : 1];
+        T f2 = T(0);
+        int st2 = 0;
+        if constexpr (D > 1) point_weights<T, W>(rq.v[1], g.B[1], ke, ts1, k1);
+        else k1[0] = T(1);
+        if constexpr (D > 2) {
+          T v2 = rq.v[2];
+          int il2 = min((int)v2, g.B[2] - 1);
+          f2 = v2 - T(il2);
+          st2 = stencil_step<W>(f2);
+          ts2 = il2 + st2;
+        }
+        const C cv = sc[q];
+        const T cr = cv.x * scale, ci = cv.y * scale;
+        const int base = ts0 + T0 * ts1 + T01 * ts2;
+        constexpr int W1 = (D > 1) ? W : 1;
+        constexpr int W2 = (D > 2) ? W : 1;
+  #pragma unroll 1
+        for (int l2 = part; l2 < W2; l2 += tpp) {
+          T k2 = T(1);
+          if constexpr (D > 2) k2 = kernel_node<T, W>(ke, l2, st2, f2);
+          const T cr2 = cr * k2, ci2 = ci * k2;
+  #pragma unroll
+          for (int l1 = 0; l1 < W1; ++l1) {
+            const T cr1 = cr2 * k1[l1], ci1 = ci2 * k1[l1];
+            I* pr = tre + base + l1 * T0 + l2 * T01;
+            I* pi = tim + base + l1 * T0 + l2 * T01;
+  #pragma unroll
+            for (int l0 = 0; l0 < W; ++l0) {
+              F::add(pr + l0, F::bits(F::quant_fma(cr1, k0[l0])));
+              F::add(pi + l0, F::bits(F::quant_fma(ci1, k0[l0])));
+            }
           }
         }
       }
-    }
-    __syncthreads();
+      __syncthreads();
 
-    // add the tile into the fine grid, wrapping periodically; rows of the
-    // tile are spread over the warps, a warp's lanes walk along x
-    int org[3];
-    tile_origin(s_geo, bin, org);
-    flush_tile<T>(s_geo, org, tre, tim, inv, grid + s_goff);
-    __syncthreads();
+      // add the tile into the fine grid, wrapping periodically; rows of the
+      // tile are spread over the warps, a warp's lanes walk along x
+      int org[3];
+      tile_origin(s_geo, bin, org);
+      flush_tile<T>(s_geo, org, tre, tim, inv, grid + s_goff);
+      __syncthreads();
+    }  // pass
   }
 }
 
@@ -1102,6 +1171,12 @@ __global__ void __launch_bounds__(256) k_interp_sparse(Geom g, const __grid_cons
   }
 }
 
+}  // namespace nufft
+
+#include "spread_interp_q.cuh"
+
+namespace nufft {
+
 // shared-memory bytes of each kernel
 template <typename T, int D>
 inline size_t spread_bytes(const Geom& g) {
@@ -1137,10 +1212,73 @@ inline KEval<T, W> make_keval(const Geom& g, double beta) {
   return ke;
 }
 
+// The bank-grouped kernels (spread_interp_q.cuh) run 3D complex64 transforms of even w.
+template <typename T, int D, int W>
+constexpr bool kQuad = std::is_same<T, float>::value && D == 3 && (W % 2) == 0;
+
+template <int W>
+cudaError_t run_spread_q(const Geom& g, double beta, const Sorted& s, const void* c, void* grid, int* work,
+                         const LaunchCfg& cfg, cudaStream_t st, bool configure_only, const BatchTable& bt) {
+  auto kern = k_spread_q<W>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.threads, cfg.smem);
+    if (e != cudaSuccess) return e;
+    const_cast<LaunchCfg&>(cfg).blocks = nb;  // blocks per SM; caller scales
+    return cudaSuccess;
+  }
+  const KEval<float, W> ke = make_keval<float, W>(g, beta);
+  // the tensor map covers the plan's own grid only; batches and foreign grids flush per cell
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const int use_map = (cfg.tmap != nullptr && bt.B == 0) ? 1 : 0;
+  if (use_map) memcpy(&map, cfg.tmap, sizeof(map));
+  kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(g, ke, s, reinterpret_cast<const float2*>(c),
+                                                  reinterpret_cast<float2*>(grid), work, bt, map, use_map);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.sparse_max <= 0) return e;
+  k_spread_sparse<float, 3, W><<<2 * cfg.blocks, 256, 0, st>>>(g, ke, s, reinterpret_cast<const float2*>(c),
+                                                                reinterpret_cast<float2*>(grid), bt);
+  return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t run_interp_q(const Geom& g, double beta, const Sorted& s, const void* grid, void* c, int* work,
+                         const LaunchCfg& cfg, cudaStream_t st, bool configure_only, const BatchTable& bt) {
+  auto kern = k_interp_q<W>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.threads, cfg.smem);
+    if (e != cudaSuccess) return e;
+    const_cast<LaunchCfg&>(cfg).blocks = nb;
+    return cudaSuccess;
+  }
+  const KEval<float, W> ke = make_keval<float, W>(g, beta);
+  // the tensor map covers the plan's own grid only; batches and foreign grids take per-cell copies
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const int use_map = (cfg.tmap != nullptr && bt.B == 0) ? 1 : 0;
+  if (use_map) memcpy(&map, cfg.tmap, sizeof(map));
+  kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(g, ke, s, reinterpret_cast<const float2*>(grid),
+                                                  reinterpret_cast<float2*>(c), work, bt, map, use_map);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.sparse_max <= 0) return e;
+  k_interp_sparse<float, 3, W><<<2 * cfg.blocks, 256, 0, st>>>(g, ke, s, reinterpret_cast<const float2*>(grid),
+                                                                reinterpret_cast<float2*>(c), bt);
+  return cudaGetLastError();
+}
+
 template <typename T, int D, int W>
 cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* c, void* grid,
                        int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
                        const BatchTable& bt) {
+  if constexpr (kQuad<T, D, W>) {
+    if (quad_layout(g)) return run_spread_q<W>(g, beta, s, c, grid, work, cfg, st, configure_only, bt);
+  }
   auto kern = k_spread<T, D, W>;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
@@ -1166,6 +1304,9 @@ template <typename T, int D, int W>
 cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* grid, void* c,
                        int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
                        const BatchTable& bt) {
+  if constexpr (kQuad<T, D, W>) {
+    if (quad_layout(g)) return run_interp_q<W>(g, beta, s, grid, c, work, cfg, st, configure_only, bt);
+  }
   auto kern = InterpKernel<T, D, W>::get(g.kernel == 1);
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);

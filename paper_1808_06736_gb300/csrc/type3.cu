@@ -427,7 +427,7 @@ int execute_t(nufft_plan3 p, const void* c, void* f) {
   if (cudaMemsetAsync(p->grid, 0, gbytes, p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
   if (M > 0) {
     if (cudaMemsetAsync(p->small + 2, 0, sizeof(int), p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
-    Sorted so{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3};
+    Sorted so{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3, p->small};
     if (launch_spread(p->dbl, p->g, p->beta, so, p->cpre, p->grid, p->small + 2, p->scfg, p->stream) != cudaSuccess)
       return NUFFT_ERR_CUDA;
   }

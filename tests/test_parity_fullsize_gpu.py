@@ -17,8 +17,8 @@ import nufft_inputs as I
 
 pytestmark = pytest.mark.gpu
 
-N_MODES = 24    # sampled modes for type 1
-N_TARGETS = 64  # sampled points for type 2
+N_MODES = 200     # sampled modes for type 1 (each an O(M) exact sum)
+N_TARGETS = 2000  # sampled points for type 2 (each an O(N^d) exact sum)
 
 
 @pytest.fixture(scope="module")
