@@ -128,6 +128,29 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
 int nufft_setpts(nufft_plan plan, int64_t M, const void* x, const void* y, const void* z);
 
 /*
+ * nufft_setpts_from -- give plan dst the points src has binned, without binning
+ * them again.  The bin sort of Sec. 5.1 depends on the points, the fine grid
+ * and the bins only, so a type-1 and a type-2 plan on the same points (or two
+ * plans of one type) can share it; typical use: setpts on a type-1 plan, then
+ * nufft_setpts_from(type-2 plan, type-1 plan).
+ *
+ * The two plans must have the same device, precision, dimension, fine grid
+ * n_i, bin extents (opts.bin_size), largest subproblem (opts.max_subprob) and
+ * per-warp threshold (opts.sparse_max); isign, type, ntransf, eps with the
+ * same grid and kernel options may differ.  The binned points are shared, not
+ * copied: neither plan may be destroyed from under the other (both keep them
+ * alive), and a later nufft_setpts on either plan gives that plan a new set,
+ * leaving the other's unchanged.  No device work is enqueued; dst's executes
+ * must be ordered after src's setpts (same stream, or an event) by the caller.
+ * Points outside [-3 pi, 3 pi] (opts.chkbnds) are reported by src's
+ * nufft_get_status only.
+ *
+ * Returns NUFFT_OK; NUFFT_ERR_BAD_ARG (NULL plan, or the plans differ in any
+ * of the above); NUFFT_ERR_NOT_SET (src has no points).
+ */
+int nufft_setpts_from(nufft_plan dst, nufft_plan src);
+
+/*
  * Run the ntransf transforms on device arrays c (ntransf * M complex) and f
  * (ntransf * N_1 ... N_d complex).  Type 1 reads c and writes f (spread,
  * Eq. (bl); FFT, Eq. (dft1); truncate and correct, Eq. (pb1)).  Type 2 reads

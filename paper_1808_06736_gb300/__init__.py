@@ -72,6 +72,7 @@ def _L():
     lib.nufft_makeplan.argtypes = [i32, i32, pi64, i32, i32, dbl, i32, vp, ctypes.POINTER(nufft_opts),
                                    ctypes.POINTER(vp)]
     lib.nufft_setpts.argtypes = [vp, i64, vp, vp, vp]
+    lib.nufft_setpts_from.argtypes = [vp, vp]
     lib.nufft_execute.argtypes = [vp, vp, vp]
     lib.nufft_execute_grad.argtypes = [vp, vp, vp, vp]
     lib.nufft_destroy.argtypes = [vp]
@@ -131,6 +132,10 @@ def nufft_makeplan(type_: int, dim: int, nmodes, isign: int, ntransf: int, eps: 
 
 def nufft_setpts(plan, M: int, x: int, y: int, z: int) -> int:
     return _L().nufft_setpts(plan, int(M), ctypes.c_void_p(x or 0), ctypes.c_void_p(y or 0), ctypes.c_void_p(z or 0))
+
+
+def nufft_setpts_from(dst, src) -> int:
+    return _L().nufft_setpts_from(dst, src)
 
 
 def nufft_execute(plan, c: int, f: int) -> int:
@@ -414,6 +419,19 @@ class Plan:
             raise NufftError(st, "nufft_setpts")
         self.M = M
         self._keep = tuple(dev)
+        return self
+
+    def setpts_from(self, other: "Plan"):
+        """Use the points ``other`` has binned (nufft_setpts_from): no second binning.  This
+        plan's stream waits for ``other``'s, where the binning was enqueued."""
+        torch = self._torch
+        if self.stream != other.stream:
+            self.stream.wait_stream(other.stream)
+        st = nufft_setpts_from(self._h, other._h)
+        if st < 0:
+            raise NufftError(st, "nufft_setpts_from")
+        self.M = other.M
+        self._keep = other._keep
         return self
 
     # -- transform

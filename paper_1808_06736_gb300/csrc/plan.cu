@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -25,6 +26,28 @@
 #include "nufft_internal.cuh"
 
 using namespace nufft;
+
+// The binned points setpts produces: one record per point in bin order, the subproblem list and
+// its two counts.  Plans share one set after nufft_setpts_from; a plan that sets new points while
+// its set is shared gets a set of its own first, so no plan ever overwrites points another reads.
+struct PointSet {
+  int device = 0;
+  void* rec = nullptr;
+  int* sub_bin = nullptr;
+  int* sub_pt0 = nullptr;
+  int* sub_cnt = nullptr;
+  int* counts = nullptr;  // device: [0] tiled subproblems, [1] per-warp subproblems
+  int64_t Mcap = 0, subcap = 0;
+  ~PointSet() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(device);
+    void* bufs[] = {rec, sub_bin, sub_pt0, sub_cnt, counts};
+    for (void* b : bufs)
+      if (b) cudaFree(b);
+    cudaSetDevice(dev);
+  }
+};
 
 struct nufft_plan_s {
   int type = 0, dim = 0, isign = 0, ntransf = 1, prec = 0;
@@ -47,14 +70,9 @@ struct nufft_plan_s {
   int* cursor = nullptr;  // scatter cursors, nrep * nbins (replica-major)
   int* rep_count = nullptr;  // replicated bin counters, nrep * nbins (nrep > 1)
   int nrep = 1;
-  int* small = nullptr;  // [0] error word, [1] tiled subproblems, [2] work counter, [3] sparse subproblems
+  int* small = nullptr;  // [0] error word, [2] work counter of the spread / interp kernels
   int64_t M = -1;
-  int64_t Mcap = 0;
-  void* rec = nullptr;
-  int64_t subcap = 0;
-  int* sub_bin = nullptr;
-  int* sub_pt0 = nullptr;
-  int* sub_cnt = nullptr;
+  std::shared_ptr<PointSet> ps;  // binned points (possibly shared with other plans)
   cufftHandle fft = 0;
   bool fft_ok = false;
   alignas(64) unsigned char tmap[128];  // CUtensorMap over grid for the interpolation's tile loads
@@ -262,6 +280,59 @@ void choose_bins(Geom& g, bool dbl, const nufft_opts& o) {
 int sparse_max_of(const nufft_opts& o) {
   if (o.sparse_max < 0) return 0;
   return o.sparse_max == 0 ? 32 : std::min(o.sparse_max, 32);
+}
+
+// a new, empty point set on the plan's device
+int new_point_set(nufft_plan p) {
+  auto ps = std::make_shared<PointSet>();
+  ps->device = p->device;
+  if (cudaMalloc((void**)&ps->counts, 2 * sizeof(int)) != cudaSuccess) {
+    ps->counts = nullptr;
+    return NUFFT_ERR_ALLOC;
+  }
+  if (cudaMemsetAsync(ps->counts, 0, 2 * sizeof(int), p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
+  p->ps = ps;
+  return NUFFT_OK;
+}
+
+// room for mcap points in the plan's own (unshared) point set
+int reserve_points(nufft_plan p, int64_t mcap) {
+  if (p->ps.use_count() > 1) {
+    int st = new_point_set(p);
+    if (st != NUFFT_OK) return st;
+  }
+  PointSet& ps = *p->ps;
+  const Geom& g = p->g;
+  if (mcap > ps.Mcap) {
+    cudaFree(ps.rec);
+    ps.rec = nullptr;
+    ps.Mcap = 0;
+    size_t rsz = p->dbl ? sizeof(RecD) : sizeof(RecF);
+    if (cudaMalloc(&ps.rec, rsz * (size_t)std::max<int64_t>(mcap, 1)) != cudaSuccess) {
+      ps.rec = nullptr;
+      return NUFFT_ERR_ALLOC;
+    }
+    ps.Mcap = mcap;
+  }
+  int64_t need = std::min<int64_t>(g.nbins, mcap) + mcap / g.maxsub + 1;
+  if (need > ps.subcap) {
+    cudaFree(ps.sub_bin);
+    cudaFree(ps.sub_pt0);
+    cudaFree(ps.sub_cnt);
+    ps.sub_bin = ps.sub_pt0 = ps.sub_cnt = nullptr;
+    ps.subcap = 0;
+    if (cudaMalloc((void**)&ps.sub_bin, sizeof(int) * (size_t)need) != cudaSuccess ||
+        cudaMalloc((void**)&ps.sub_pt0, sizeof(int) * (size_t)need) != cudaSuccess ||
+        cudaMalloc((void**)&ps.sub_cnt, sizeof(int) * (size_t)need) != cudaSuccess)
+      return NUFFT_ERR_ALLOC;
+    ps.subcap = need;
+  }
+  return NUFFT_OK;
+}
+
+Sorted sorted_of(nufft_plan p) {
+  const PointSet& ps = *p->ps;
+  return Sorted{ps.rec, ps.sub_bin, ps.sub_pt0, ps.sub_cnt, ps.counts, ps.counts + 1, p->small};
 }
 
 int fail(nufft_plan p, int code) {
@@ -535,6 +606,7 @@ int nufft_makeplan(int type, int dim, const int64_t* nmodes, int isign, int ntra
       dev_alloc(&p->small, sizeof(int) * 4) != cudaSuccess)
     return fail(p, NUFFT_ERR_ALLOC);
   if (cudaMemset(p->small, 0, sizeof(int) * 4) != cudaSuccess) return fail(p, NUFFT_ERR_CUDA);
+  if (new_point_set(p) != NUFFT_OK) return fail(p, NUFFT_ERR_ALLOC);
 
   // both launch shapes: the serving layer runs a plan's adjoint (type 1 on a type-2 plan)
   if (spread_config(p->dbl, g, threads, &p->spread_cfg) != cudaSuccess ||
@@ -568,36 +640,35 @@ int nufft_setpts(nufft_plan p, int64_t M, const void* x, const void* y, const vo
   if (M >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_TOO_BIG;
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
   const Geom& g = p->g;
-  if (M > p->Mcap) {
-    cudaFree(p->rec);
-    p->rec = nullptr;
-    p->Mcap = 0;
-    size_t rsz = p->dbl ? sizeof(RecD) : sizeof(RecF);
-    if (dev_alloc(&p->rec, rsz * (size_t)M) != cudaSuccess) return NUFFT_ERR_ALLOC;
-    p->Mcap = M;
-  }
-  int64_t need = std::min<int64_t>(g.nbins, M) + M / g.maxsub + 1;
-  if (need > p->subcap) {
-    cudaFree(p->sub_bin);
-    cudaFree(p->sub_pt0);
-    cudaFree(p->sub_cnt);
-    p->sub_bin = p->sub_pt0 = p->sub_cnt = nullptr;
-    p->subcap = 0;
-    if (dev_alloc(&p->sub_bin, sizeof(int) * (size_t)need) != cudaSuccess ||
-        dev_alloc(&p->sub_pt0, sizeof(int) * (size_t)need) != cudaSuccess ||
-        dev_alloc(&p->sub_cnt, sizeof(int) * (size_t)need) != cudaSuccess)
-      return NUFFT_ERR_ALLOC;
-    p->subcap = need;
-  }
+  int rc = reserve_points(p, M);
+  if (rc != NUFFT_OK) return rc;
+  PointSet& ps = *p->ps;
   FoldConst fc = make_fold_const(g);
   cudaError_t e = launch_setpts(p->dbl, g, fc, M, x, y, z, p->opts.chkbnds, p->bin_count, p->bin_start,
-                                p->sub_first, p->cursor, p->rec, p->sub_bin, p->sub_pt0,
-                                p->sub_cnt, p->small + 1, p->small + 3, p->small + 0, p->stream,
+                                p->sub_first, p->cursor, ps.rec, ps.sub_bin, ps.sub_pt0,
+                                ps.sub_cnt, ps.counts, ps.counts + 1, p->small + 0, p->stream,
                                 p->ev_ok ? p->ev : nullptr, BatchTable{nullptr, nullptr, nullptr, nullptr, nullptr, 0},
                                 g.nbins, Replicas{p->nrep, p->rep_count, p->cursor});
   if (e != cudaSuccess) return NUFFT_ERR_CUDA;
   p->M = M;
   p->last_steps = 1;
+  return NUFFT_OK;
+}
+
+int nufft_setpts_from(nufft_plan dst, nufft_plan src) {
+  if (!dst || !src) return NUFFT_ERR_BAD_ARG;
+  if (src->M < 0) return NUFFT_ERR_NOT_SET;
+  const Geom& a = dst->g;
+  const Geom& b = src->g;
+  // the binning depends on the fine grid, the bin extents, the subproblem limits and the precision
+  bool same = dst->device == src->device && dst->dbl == src->dbl && a.d == b.d && a.maxsub == b.maxsub &&
+              a.sparse_max == b.sparse_max;
+  for (int i = 0; i < 3; ++i) same = same && a.n[i] == b.n[i] && a.B[i] == b.B[i];
+  if (!same) return NUFFT_ERR_BAD_ARG;
+  if (dst == src) return NUFFT_OK;
+  dst->ps = src->ps;
+  dst->M = src->M;
+  dst->last_steps = 0;
   return NUFFT_OK;
 }
 
@@ -616,7 +687,7 @@ int plan_execute_as(nufft_plan p, int type, int isign, void* c, void* f) {
   if (!f || (p->M > 0 && !c)) return NUFFT_ERR_BAD_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
   const Geom& g = p->g;
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3, p->small};
+  Sorted s = sorted_of(p);
   ModeGeom mg;
   mg.d = p->dim;
   mg.modeord = p->opts.modeord ? 1 : 0;
@@ -667,7 +738,7 @@ int plan_execute_grad(nufft_plan p, void* c, void* dc, const void* f) {
     int threads = p->opts.threads > 0 ? p->opts.threads : 256;
     if (grad_config(p->dbl, g, threads, &p->grad_cfg) != cudaSuccess) return NUFFT_ERR_CUDA;
   }
-  Sorted s{p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt, p->small + 1, p->small + 3, p->small};
+  Sorted s = sorted_of(p);
   ModeGeom mg;
   mg.d = p->dim;
   mg.modeord = p->opts.modeord ? 1 : 0;
@@ -715,29 +786,7 @@ int plan_reserve(nufft_plan p, int64_t mcap) {
   if (!p || mcap < 0) return NUFFT_ERR_BAD_ARG;
   if (mcap >= ((int64_t)1 << 31) - 1) return NUFFT_ERR_TOO_BIG;
   if (cudaSetDevice(p->device) != cudaSuccess) return NUFFT_ERR_CUDA;
-  const Geom& g = p->g;
-  if (mcap > p->Mcap) {
-    cudaFree(p->rec);
-    p->rec = nullptr;
-    p->Mcap = 0;
-    size_t rsz = p->dbl ? sizeof(RecD) : sizeof(RecF);
-    if (dev_alloc(&p->rec, rsz * (size_t)mcap) != cudaSuccess) return NUFFT_ERR_ALLOC;
-    p->Mcap = mcap;
-  }
-  int64_t need = std::min<int64_t>(g.nbins, mcap) + mcap / g.maxsub + 1;
-  if (need > p->subcap) {
-    cudaFree(p->sub_bin);
-    cudaFree(p->sub_pt0);
-    cudaFree(p->sub_cnt);
-    p->sub_bin = p->sub_pt0 = p->sub_cnt = nullptr;
-    p->subcap = 0;
-    if (dev_alloc(&p->sub_bin, sizeof(int) * (size_t)need) != cudaSuccess ||
-        dev_alloc(&p->sub_pt0, sizeof(int) * (size_t)need) != cudaSuccess ||
-        dev_alloc(&p->sub_cnt, sizeof(int) * (size_t)need) != cudaSuccess)
-      return NUFFT_ERR_ALLOC;
-    p->subcap = need;
-  }
-  return NUFFT_OK;
+  return reserve_points(p, mcap);
 }
 
 // Device bytes a plan holds: its buffers plus cuFFT's work area.
@@ -746,7 +795,7 @@ size_t plan_device_bytes(nufft_plan p) {
   size_t rs = p->dbl ? 8 : 4, cs = p->csize;
   size_t b = (size_t)p->ngrid * cs + (3 + 2 * (size_t)p->nrep) * sizeof(int) * (size_t)p->g.nbins + 4 * sizeof(int);
   for (int i = 0; i < 3; ++i) b += (size_t)p->N[i] * rs;
-  b += (size_t)p->Mcap * (p->dbl ? sizeof(RecD) : sizeof(RecF)) + 3 * sizeof(int) * (size_t)p->subcap;
+  if (p->ps) b += (size_t)p->ps->Mcap * (p->dbl ? sizeof(RecD) : sizeof(RecF)) + 3 * sizeof(int) * (size_t)p->ps->subcap;
   size_t ws = 0;
   if (p->fft_ok && cufftGetSize(p->fft, &ws) == CUFFT_SUCCESS) b += ws;
   return b;
@@ -879,9 +928,10 @@ int nufft_destroy(nufft_plan p) {
   if (p->ev_ok)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(p->ev[i]);
   void* bufs[] = {p->grid, p->pk[0], p->pk[1], p->pk[2], p->bin_count, p->bin_start, p->sub_first,
-                  p->cursor, p->rep_count, p->small, p->rec, p->sub_bin, p->sub_pt0, p->sub_cnt};
+                  p->cursor, p->rep_count, p->small};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  p->ps.reset();  // freed here unless another plan still shares it
   cudaSetDevice(dev);
   delete p;
   return NUFFT_OK;
@@ -931,7 +981,7 @@ int nufft_plan_info(nufft_plan p, int* w, double* beta, int64_t* n, int* bins, i
     if (p->M >= 0) {
       if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NUFFT_ERR_CUDA;
       int v = 0;
-      if (cudaMemcpy(&v, p->small + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NUFFT_ERR_CUDA;
+      if (cudaMemcpy(&v, p->ps->counts, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NUFFT_ERR_CUDA;
       *nsub = v;
     }
   }
