@@ -258,7 +258,6 @@ __global__ void __launch_bounds__(256, 4) k_spread_q(Geom g, const __grid_consta
   const bool tma_ok = use_tmap && bt.B == 0 && qtile <= kFlushCells * (int)blockDim.x;
   for (;;) {
     if (threadIdx.x == 0) {
-      if (tma_ok) bulk_wait_read();  // the previous tile's bulk reduction has read it
       next_subproblem(g, s, bt, work, &s_sub, &s_bin, &s_goff, &s_geo);
       s_maxbits = 0;
       s_nsmall = 0;
@@ -276,10 +275,6 @@ __global__ void __launch_bounds__(256, 4) k_spread_q(Geom g, const __grid_consta
     tile_origin(s_geo, bin, org);
     const int xsh = tile_xsh(org);
 
-    for (int t = threadIdx.x; t < qtile; t += blockDim.x) {
-      tre[t] = 0;
-      tim[t] = 0;
-    }
     float mloc = 0.f;
     for (int q0 = threadIdx.x; q0 < cnt; q0 += 4 * blockDim.x) {
       RecF r[4];
@@ -310,6 +305,15 @@ __global__ void __launch_bounds__(256, 4) k_spread_q(Geom g, const __grid_consta
     // packing cost more than the conflicts it saves (measured: 12.48 -> 12.00 ms on 1e8 points)
     const int nslots = bucket_order<float, 3, 8, false>(cnt, st, hist, &s_nslots);
 
+    // the tile is zeroed only now, so the previous tile's bulk reduction reads it while this
+    // subproblem's points are staged and ordered; plan_passes' barrier orders the zeros
+    // before the main loop
+    if (tma_ok && threadIdx.x == 0) bulk_wait_read();
+    __syncthreads();
+    for (int t = threadIdx.x; t < qtile; t += blockDim.x) {
+      tre[t] = 0;
+      tim[t] = 0;
+    }
     const float maxabs = __int_as_float(s_maxbits);
     const double K = fmin(Fixed<float>::KMAX, floor(Fixed<float>::IMAX / (double)cnt) - 1.0);
     float thr, smax;
