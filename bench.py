@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="execution slots of the request loop")
     ap.add_argument("--serve-budget-gb", type=int, default=64, help="device-memory budget of the request loop")
     ap.add_argument("--no-serving", action="store_true", help="leave the serving summary out of the 3d line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave the other workloads (3D clustered, 3D complex128, 2D, batched 2D) out of the 3d line")
     return ap.parse_args()
 
 
@@ -399,6 +401,106 @@ def run_cuda(args, ws, rank, local):
             "separate_binning": separate}
 
 
+# ---------------------------------------------------- the other workloads
+EXTRA_CONFIGS = [
+    # (name, d, N per dimension, M, precision, eps, point distribution)
+    ("3d_c64_clustered", 3, 256, 100_000_000, "c64", 1e-5, "clustered"),
+    ("3d_c128_uniform", 3, 256, 30_000_000, "c128", 1e-9, "uniform"),
+    ("2d_c64_uniform", 2, 1024, 10_000_000, "c64", 1e-5, "uniform"),
+    ("2d_c64_clustered", 2, 1024, 10_000_000, "c64", 1e-5, "clustered"),
+    ("2d_c128_uniform", 2, 1024, 10_000_000, "c128", 1e-9, "uniform"),
+    ("2d_c128_clustered", 2, 1024, 10_000_000, "c128", 1e-9, "clustered"),
+]
+
+
+def measure_config(name, d, N, M, prec, eps, kind, steps, warmup, peaks):
+    """One configuration of the workload list: the step of the headline (setpts + type 1, the
+    type-2 plan on the same binned points + type 2), timed with CUDA events over ``steps``
+    steps after ``warmup``; per-kernel medians from the plans' debug events; the dominant
+    kernel's algorithmic flops against the FP32 rate (complex64; derived from unit counts)
+    or the nominal FP64 rate (complex128)."""
+    import torch
+
+    import nufft_inputs as I
+    import paper_1808_06736_gb300 as pkg
+
+    dev = torch.device("cuda", 0)
+    Ns = [N] * d
+    cdt = torch.complex128 if prec == "c128" else torch.complex64
+    rdt = torch.float64 if prec == "c128" else torch.float32
+    seed = 3000 + 10 * d + (1 if kind == "clustered" else 0) + (2 if prec == "c128" else 0)
+    xs = I.torch_points(seed, M, d, kind, dev, rdt)
+    c = I.torch_complex_normal(seed + 1, M, dev, cdt)
+    f = I.torch_complex_normal(seed + 2, N ** d, dev, cdt)
+    p1 = pkg.Plan(1, Ns, eps=eps, isign=1, dtype=cdt, device=dev, debug=1)
+    p2 = pkg.Plan(2, Ns, eps=eps, isign=-1, dtype=cdt, device=dev, debug=1)
+    fout = torch.empty((1,) + tuple(Ns), dtype=cdt, device=dev)
+    cout = torch.empty((1, M), dtype=cdt, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    slots = {k: [] for k in ("fold", "scan", "scatter", "spread", "fft1", "deconv", "precorrect", "fft2", "interp")}
+
+    def step(record):
+        p1.setpts(*xs)
+        if record:
+            t = p1.timings()
+        p1.execute(c, out=fout)
+        if record:
+            t1 = p1.timings()
+        p2.setpts_from(p1)
+        p2.execute(f, out=cout)
+        if record:
+            t2 = p2.timings()
+            slots["fold"].append(t[0]); slots["scan"].append(t[1]); slots["scatter"].append(t[2])
+            slots["spread"].append(t1[3]); slots["fft1"].append(t1[4]); slots["deconv"].append(t1[5])
+            slots["precorrect"].append(t2[3]); slots["fft2"].append(t2[4]); slots["interp"].append(t2[5])
+
+    for _ in range(warmup):
+        step(False)
+    for _ in range(3):
+        step(True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step(False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    st = (p1.status(), p2.status())
+    w = p1.info["w"]
+    p1.close()
+    p2.close()
+    if st != (0, 0):
+        raise RuntimeError("%s: device status %s" % (name, st))
+    med = {k: round(statistics.median(v), 4) for k, v in slots.items()}
+    dom = max(("spread", "interp"), key=lambda k: med[k])
+    flops = algorithmic_units(d, w) * M
+    achieved = flops / (med[dom] * 1e-3) / 1e12
+    if prec == "c64":
+        peak, src = peaks["fp32_derived_tflops"], "FP32, derived from unit counts"
+    else:
+        peak, src = FP64_NOMINAL_TFLOPS, "FP64, nominal"
+    return {"name": name, "workload": "%dD type 1 + type 2, N=%d^%d, M=%d %s points, %s, eps=%g"
+            % (d, N, d, M, kind, "complex128" if prec == "c128" else "complex64", eps),
+            "value": 2 * M / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "w": w, "kernels_ms": med,
+            "roofline": {"kernel": "k_%s" % dom, "achieved_tflops": achieved, "peak_tflops": peak,
+                         "frac": achieved / peak, "peak_source": src,
+                         "algorithmic_flops_per_point": algorithmic_units(d, w)}}
+
+
+def run_extra_configs(args, peaks):
+    """Every other configuration of the workload list, and the batched 2D workload against
+    its one-plan-per-transform comparator; each config freed before the next."""
+    import torch
+    out = []
+    for cfg in EXTRA_CONFIGS:
+        out.append(measure_config(*cfg, steps=5, warmup=2, peaks=peaks))
+        torch.cuda.empty_cache()
+    out.append(batched2d_measure(args, autotune=False))
+    torch.cuda.empty_cache()
+    return out
+
+
 # -------------------------------------------------------------- oracle arm
 def oracle_sample(args, M_sample, reps=1):
     """Time the oracle (O2, fp64, OpenMP over all host cores) on a bounded sample of the
@@ -470,7 +572,7 @@ def run_reference(args):
     return 0
 
 
-def run_batched2d(args):
+def batched2d_measure(args, autotune=True):
     """1024 independent 2D type-2 transforms, complex64, eps = 1e-5: N per transform uniform in
     {64^2, 128^2, 256^2, 512^2}, M log-uniform in [1e3, 1e6] uniform points, coefficients re/im
     N(0, 1).  Batched: one BatchPlan (one launch per step, CUDA graph).  Plain: one Plan per
@@ -515,24 +617,9 @@ def run_batched2d(args):
     assert bp.status() == 0
 
     # autotuned batch plan (bin shape, subproblem size, sparse threshold, block size)
-    t_tune = time.time()
-    opts, tune_best, tune_default = pkg.tune_batch(2, modes, xs, f, offs, eps=args.eps, isign=-1, reps=2)
-    t_tune = time.time() - t_tune
-    bt = pkg.BatchPlan(2, modes, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev, **opts)
-    for _ in range(args.warmup):
-        bt.setpts(*xs, offsets=offs)
-        bt.execute(f, out=cout)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        bt.setpts(*xs, offsets=offs)
-        bt.execute(f, out=cout)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_t = e0.elapsed_time(e1) / args.steps
-    assert bt.status() == 0
-    bt.close()
-
+    ms_t, opts, tune_best, tune_default, t_tune = None, None, None, None, None
+    if autotune:
+        ms_t, opts, tune_best, tune_default, t_tune = batched2d_tuned(args, modes, xs, f, offs, cout, e0, e1, stream)
     plans = [pkg.Plan(2, m, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev) for m in modes]
     moffs = bp.mode_offsets
     couts = [cout[int(offs[t]):int(offs[t + 1])] for t in range(B)]
@@ -556,18 +643,52 @@ def run_batched2d(args):
     for p in plans:
         p.close()
     bp.close()
-    ms_best = min(ms_b, ms_t)
-    line = {"metric": "batched 2D type-2 NU points/s (%d transforms, eps=%g, fp32)" % (B, args.eps),
-            "value": Mtot / (ms_best * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_best, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "batched2d", "transforms": B, "modes": "uniform in {64,128,256,512}^2",
-                       "M": "log-uniform in [1e3, 1e6]", "points_total": Mtot, "step": "setpts + execute of all"},
-            "default_options": {"value": Mtot / (ms_b * 1e-3), "ms_per_step": ms_b},
-            "autotuned": {"value": Mtot / (ms_t * 1e-3), "ms_per_step": ms_t, "options": opts,
-                          "tuner_best_ms": tune_best, "tuner_default_ms": tune_default, "tuning_s": t_tune},
-            "plain": {"value": Mtot / (ms_p * 1e-3), "ms_per_step": ms_p, "path": "one Plan per transform"},
-            "speedup_vs_plain": ms_p / ms_best}
+    ms_best = ms_b if ms_t is None else min(ms_b, ms_t)
+    res = {"name": "batched2d", "metric": "batched 2D type-2 NU points/s (%d transforms, eps=%g, fp32)" % (B, args.eps),
+           "value": Mtot / (ms_best * 1e-3), "unit": UNIT, "ms_per_step": ms_best,
+           "config": {"workload": "batched2d", "transforms": B, "modes": "uniform in {64,128,256,512}^2",
+                      "M": "log-uniform in [1e3, 1e6]", "points_total": Mtot, "step": "setpts + execute of all"},
+           "default_options": {"value": Mtot / (ms_b * 1e-3), "ms_per_step": ms_b},
+           "plain": {"value": Mtot / (ms_p * 1e-3), "ms_per_step": ms_p, "path": "one Plan per transform"},
+           "speedup_vs_plain": ms_p / ms_best}
+    if ms_t is not None:
+        res["autotuned"] = {"value": Mtot / (ms_t * 1e-3), "ms_per_step": ms_t, "options": opts,
+                            "tuner_best_ms": tune_best, "tuner_default_ms": tune_default, "tuning_s": t_tune}
+    return res
+
+
+def batched2d_tuned(args, modes, xs, f, offs, cout, e0, e1, stream):
+    """The batched workload on an autotuned batch plan: (ms per step, options, tuner figures)."""
+    import torch
+
+    import paper_1808_06736_gb300 as pkg
+    dev = xs[0].device
+    t_tune = time.time()
+    opts, tune_best, tune_default = pkg.tune_batch(2, modes, xs, f, offs, eps=args.eps, isign=-1, reps=2)
+    t_tune = time.time() - t_tune
+    bt = pkg.BatchPlan(2, modes, eps=args.eps, isign=-1, dtype=torch.complex64, device=dev, **opts)
+    for _ in range(args.warmup):
+        bt.setpts(*xs, offsets=offs)
+        bt.execute(f, out=cout)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.setpts(*xs, offsets=offs)
+        bt.execute(f, out=cout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / args.steps
+    assert bt.status() == 0
+    bt.close()
+    return ms_t, opts, tune_best, tune_default, t_tune
+
+
+def run_batched2d(args):
+    r = batched2d_measure(args, autotune=True)
+    line = {"metric": r["metric"], "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": r["config"]}
+    line.update({k: v for k, v in r.items() if k not in ("metric", "value", "ms_per_step", "config", "name")})
     print(json.dumps(line))
     return 0
 
@@ -831,6 +952,13 @@ def main():
     serving = None
     if not args.no_serving and ws == 1:
         serving = run_serving(args)
+    configs = None
+    if not args.no_configs and ws == 1:
+        import torch
+        pk = dict(r["peaks"])
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        pk["fp32_derived_tflops"] = sms * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+        configs = run_extra_configs(args, pk)
     cpu = None
     if not args.no_cpu:
         reps = 3
@@ -844,7 +972,8 @@ def main():
             "config": config_dict(args),
             "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
             "gpu_launches": r["gpu_launches"], "kernels_ms": r["kernels_ms"], "execute_only": r["execute_only"],
-            "measured_peaks": r["peaks"], "separate_binning": r["separate_binning"], "serving": serving}
+            "measured_peaks": r["peaks"], "separate_binning": r["separate_binning"], "serving": serving,
+            "configs": configs}
     print(json.dumps(line))
     return 0
 
