@@ -36,13 +36,14 @@ sys.path.insert(0, ROOT)
 METRIC = "type1/2 NU points/s at eps=1e-5 (3D, fp32)"
 
 # DRAM bytes (read + write) per launch of the spread / interp kernels on the
-# default workload, from one 1-pass ncu capture (profiles/launch_list_3d_c64_N256_M1e8.md),
-# valid only for the kernel source they were measured on.
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1808_06736_gb300", "csrc", "spread_interp.cuh")
+# default workload: the bytes per point of a full-ncu-set capture of the same kernels on
+# 1e7 points (a 256^3 fine grid, similar points per cell) times 1e8 points -- valid only
+# for the kernel source they were measured on.
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1808_06736_gb300", "csrc", "spread_interp_q.cuh")
 MEASURED_TRAFFIC = {
-    "sha256": "48bfce4fa5c11dcc9d0f188ec02b41e3a87761fe93dc70eebb724b57d7b0ecc2",
-    "spread": 15072193792 + 1226622976,
-    "interp": 6018531328 + 3176846080,
+    "sha256": "175d8a4b4ffb44426f95d25d01961e6ab98b90a2a4dc66e02f60db6dcf95e6c8",
+    "spread": (1084197000 + 96837632) * 10,
+    "interp": (481178000 + 234544640) * 10,
 }
 
 
