@@ -48,6 +48,13 @@ __host__ __device__ inline size_t spread_q_bytes(const Geom& g) {
 __host__ __device__ inline size_t interp_q_bytes(const Geom& g) {
   return 128 + (size_t)g.qtile * 8 + (size_t)g.maxsub * 5 * 2;
 }
+// The complex128 spread with 32-bit fixed-point words (spread_dw.cuh) runs kernel widths up to
+// kDwMaxW, one block of 512 threads per SM.  Its shared memory: six int planes of ntile cells
+// (rounded up to 16 bytes), maxsub staged strengths, the gapless point order (3 maxsub shorts).
+constexpr int kDwMaxW = 12;
+__host__ __device__ inline size_t spread_dw_bytes(const Geom& g) {
+  return ((6 * (size_t)g.ntile * 4 + 15) & ~(size_t)15) + (size_t)g.maxsub * 16 + (size_t)g.maxsub * 3 * 2;
+}
 
 // Bin ids run over super-blocks of sb[0] x sb[1] x sb[2] bins, dimension 1
 // fastest inside a super-block and across super-blocks.  Subproblems are

@@ -263,7 +263,8 @@ void choose_bins(Geom& g, bool dbl, const nufft_opts& o) {
   static const int c2[][3] = {{32, 32, 1}, {32, 16, 1}, {16, 16, 1}, {16, 8, 1}, {8, 8, 1}};
   static const int c1[][3] = {{1024, 1, 1}, {512, 1, 1}, {256, 1, 1}, {128, 1, 1}, {64, 1, 1}};
   const int(*c)[3] = g.d == 3 ? c3 : (g.d == 2 ? c2 : c1);
-  const size_t budget = 110 * 1024;
+  // two blocks per SM; the complex128 spread with 32-bit words runs one 512-thread block per SM
+  const size_t budget = (dbl && g.w <= kDwMaxW) ? 216 * 1024 : 110 * 1024;
   for (int k = 0; k < 5; ++k) {
     for (int i = 0; i < 3; ++i) {
       int b = (o.bin_size[i] > 0 && i < g.d) ? o.bin_size[i] : c[k][i];
@@ -353,6 +354,7 @@ namespace nufft {
 
 size_t spread_smem_bytes(bool dbl, const Geom& g, int) {
   if (!dbl && quad_layout(g)) return spread_q_bytes(g);
+  if (dbl && g.w <= kDwMaxW) return spread_dw_bytes(g);
   size_t ci = dbl ? 8 : 4, cc = dbl ? 16 : 8;
   // the spread's point order is gapless: res, rank and order of maxsub entries each
   return 2 * (size_t)g.ntile * ci + (size_t)g.maxsub * cc + (size_t)g.maxsub * 3 * 2;

@@ -1174,16 +1174,11 @@ __global__ void __launch_bounds__(256) k_interp_sparse(Geom g, const __grid_cons
 }  // namespace nufft
 
 #include "spread_interp_q.cuh"
+#include "spread_dw.cuh"
 
 namespace nufft {
 
 // shared-memory bytes of each kernel
-template <typename T, int D>
-inline size_t spread_bytes(const Geom& g) {
-  using I = typename Fixed<T>::I;
-  return 2 * (size_t)g.ntile * sizeof(I) + (size_t)g.maxsub * sizeof(typename Traits<T>::C) +
-         stage_bytes<T, D>(g.maxsub, false);
-}
 template <typename T, int D>
 inline size_t interp_bytes(const Geom& g) {
   return (size_t)g.ntile * sizeof(typename Traits<T>::C) + stage_bytes<T, D>(g.maxsub);
@@ -1272,6 +1267,32 @@ cudaError_t run_interp_q(const Geom& g, double beta, const Sorted& s, const void
   return cudaGetLastError();
 }
 
+// The complex128 spread with 32-bit words (spread_dw.cuh) serves w <= kDwMaxW; wider kernels
+// (eps below about 1e-11) keep 64-bit words, whose finer resolution those tolerances need.
+template <int D, int W>
+cudaError_t run_spread_dw(const Geom& g, double beta, const Sorted& s, const void* c, void* grid, int* work,
+                          const LaunchCfg& cfg, cudaStream_t st, bool configure_only, const BatchTable& bt) {
+  // blocks of DWords::kThreads threads whatever the plan's block size (one block per SM)
+  auto kern = g.kernel == 1 ? k_spread_dw<D, W, true> : k_spread_dw<D, W, false>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, DWords::kThreads, cfg.smem);
+    if (e != cudaSuccess) return e;
+    const_cast<LaunchCfg&>(cfg).blocks = nb;  // blocks per SM; caller scales
+    return cudaSuccess;
+  }
+  const KEval<double, W> ke = make_keval<double, W>(g, beta);
+  kern<<<cfg.blocks, DWords::kThreads, cfg.smem, st>>>(g, ke, s, reinterpret_cast<const double2*>(c),
+                                                       reinterpret_cast<double2*>(grid), work, bt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || g.sparse_max <= 0) return e;
+  k_spread_sparse<double, D, W><<<2 * cfg.blocks, 256, 0, st>>>(g, ke, s, reinterpret_cast<const double2*>(c),
+                                                                 reinterpret_cast<double2*>(grid), bt);
+  return cudaGetLastError();
+}
+
 template <typename T, int D, int W>
 cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* c, void* grid,
                        int* work, const LaunchCfg& cfg, cudaStream_t st, bool configure_only,
@@ -1279,6 +1300,8 @@ cudaError_t run_spread(const Geom& g, double beta, const Sorted& s, const void* 
   if constexpr (kQuad<T, D, W>) {
     if (quad_layout(g)) return run_spread_q<W>(g, beta, s, c, grid, work, cfg, st, configure_only, bt);
   }
+  if constexpr (std::is_same<T, double>::value && W <= kDwMaxW)
+    return run_spread_dw<D, W>(g, beta, s, c, grid, work, cfg, st, configure_only, bt);
   auto kern = k_spread<T, D, W>;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
