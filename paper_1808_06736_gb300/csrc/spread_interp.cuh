@@ -640,17 +640,17 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_spread(Geom g, con
         const int base = ts0 + T0 * ts1 + T01 * ts2;
         constexpr int W1 = (D > 1) ? W : 1;
         constexpr int W2 = (D > 2) ? W : 1;
-  #pragma unroll 1
+#pragma unroll 1
         for (int l2 = part; l2 < W2; l2 += tpp) {
           T k2 = T(1);
           if constexpr (D > 2) k2 = kernel_node<T, W>(ke, l2, st2, f2);
           const T cr2 = cr * k2, ci2 = ci * k2;
-  #pragma unroll
+#pragma unroll
           for (int l1 = 0; l1 < W1; ++l1) {
             const T cr1 = cr2 * k1[l1], ci1 = ci2 * k1[l1];
             I* pr = tre + base + l1 * T0 + l2 * T01;
             I* pi = tim + base + l1 * T0 + l2 * T01;
-  #pragma unroll
+#pragma unroll
             for (int l0 = 0; l0 < W; ++l0) {
               F::add(pr + l0, F::bits(F::quant_fma(cr1, k0[l0])));
               F::add(pi + l0, F::bits(F::quant_fma(ci1, k0[l0])));
@@ -809,8 +809,13 @@ __device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int c
   }
 }
 
+// blocks of 512 threads: a tile of a 16x8x8 bin at w = 10 (135 KB) leaves room for one block
+// per SM, and 512 threads at up to 128 registers fill the register file
+constexpr int kInterpDfThreads = 512;
+// dynamic shared memory above which at most one block fits an SM (228 KB, 1 KB per block reserved)
+constexpr size_t kOneBlockSmem = 112 * 1024;
 template <int D, int W, bool COSH>
-__global__ void __launch_bounds__(256, 2) k_interp_df(Geom g, const __grid_constant__ KEval<double, W> ke, Sorted s, const double2* __restrict__ grid,
+__global__ void __launch_bounds__(kInterpDfThreads, 1) k_interp_df(Geom g, const __grid_constant__ KEval<double, W> ke, Sorted s, const double2* __restrict__ grid,
                                                       double2* __restrict__ c, int* __restrict__ work, BatchTable bt) {
   using Rec = typename Traits<double>::Rec;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1272,20 +1277,22 @@ cudaError_t run_interp_q(const Geom& g, double beta, const Sorted& s, const void
 template <int D, int W>
 cudaError_t run_spread_dw(const Geom& g, double beta, const Sorted& s, const void* c, void* grid, int* work,
                           const LaunchCfg& cfg, cudaStream_t st, bool configure_only, const BatchTable& bt) {
-  // blocks of DWords::kThreads threads whatever the plan's block size (one block per SM)
+  // blocks of DWords::kThreads threads when the tile leaves room for one block per SM, two blocks
+  // of 256 threads otherwise
   auto kern = g.kernel == 1 ? k_spread_dw<D, W, true> : k_spread_dw<D, W, false>;
+  const int threads = cfg.smem > kOneBlockSmem ? DWords::kThreads : 256;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, DWords::kThreads, cfg.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, cfg.smem);
     if (e != cudaSuccess) return e;
     const_cast<LaunchCfg&>(cfg).blocks = nb;  // blocks per SM; caller scales
     return cudaSuccess;
   }
   const KEval<double, W> ke = make_keval<double, W>(g, beta);
-  kern<<<cfg.blocks, DWords::kThreads, cfg.smem, st>>>(g, ke, s, reinterpret_cast<const double2*>(c),
-                                                       reinterpret_cast<double2*>(grid), work, bt);
+  kern<<<cfg.blocks, threads, cfg.smem, st>>>(g, ke, s, reinterpret_cast<const double2*>(c),
+                                              reinterpret_cast<double2*>(grid), work, bt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || g.sparse_max <= 0) return e;
   k_spread_sparse<double, D, W><<<2 * cfg.blocks, 256, 0, st>>>(g, ke, s, reinterpret_cast<const double2*>(c),
@@ -1331,16 +1338,20 @@ cudaError_t run_interp(const Geom& g, double beta, const Sorted& s, const void* 
     if (quad_layout(g)) return run_interp_q<W>(g, beta, s, grid, c, work, cfg, st, configure_only, bt);
   }
   auto kern = InterpKernel<T, D, W>::get(g.kernel == 1);
+  // the complex128 (double-float) interpolation: blocks of kInterpDfThreads when its tile leaves
+  // room for one block per SM, two blocks of 256 threads otherwise
+  const int threads = std::is_same<T, double>::value ? (cfg.smem > kOneBlockSmem ? kInterpDfThreads : 256)
+                                                     : cfg.threads;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.threads, cfg.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, cfg.smem);
     if (e != cudaSuccess) return e;
     const_cast<LaunchCfg&>(cfg).blocks = nb;
     return cudaSuccess;
   }
-  kern<<<cfg.blocks, cfg.threads, cfg.smem, st>>>(
+  kern<<<cfg.blocks, threads, cfg.smem, st>>>(
       g, make_keval<T, W>(g, beta), s, reinterpret_cast<const typename Traits<T>::C*>(grid),
       reinterpret_cast<typename Traits<T>::C*>(c), work, bt);
   cudaError_t e = cudaGetLastError();
