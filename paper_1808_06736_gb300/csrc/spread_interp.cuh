@@ -482,9 +482,16 @@ struct MinBlocks {
 // Thread 0 takes the next subproblem and puts its geometry in shared memory:
 // for a batch, the subproblem's transform, its grid offset and its bin id
 // within that transform.  Returns false when the work list is exhausted.
+__device__ __forceinline__ void resolve_subproblem(const Geom& g, const Sorted& s, const BatchTable& bt, int sub,
+                                                   int* s_sub, int* s_bin, long long* s_goff, Geom* s_geo);
 __device__ __forceinline__ void next_subproblem(const Geom& g, const Sorted& s, const BatchTable& bt, int* work,
                                                 int* s_sub, int* s_bin, long long* s_goff, Geom* s_geo) {
-  const int sub = atomicAdd(work, 1);
+  resolve_subproblem(g, s, bt, atomicAdd(work, 1), s_sub, s_bin, s_goff, s_geo);
+}
+// The same for a subproblem id taken from the work counter earlier (a block claims its next id
+// while it works on the current one, so the atomic's latency is hidden).
+__device__ __forceinline__ void resolve_subproblem(const Geom& g, const Sorted& s, const BatchTable& bt, int sub,
+                                                   int* s_sub, int* s_bin, long long* s_goff, Geom* s_geo) {
   *s_sub = sub;
   if (sub < *s.nsub) {
     int bin = s.sub_bin[sub];

@@ -171,6 +171,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// contiguous bulk copy of nbytes (a multiple of 16) from global to shared memory (both
+// addresses 16-byte aligned), completing on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned nbytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(nbytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // bulk tensor reduce-add of a 3D box of floats from shared memory into global memory
 // (x in floats, 16-byte aligned, not negative), in the current bulk group
 __device__ __forceinline__ void tma_reduce_add_3d(const void* src, const CUtensorMap* map, int x, int y, int z) {
@@ -427,9 +436,16 @@ __global__ void __launch_bounds__(256, 4) k_interp_q(Geom g, const __grid_consta
   const unsigned tile_bytes = (unsigned)qtile * 8u;
   unsigned phase = 0;
   if (use_tmap && threadIdx.x == 0) mbar_init(&s_bar);
+  // wrapping tiles fetched by row copies (the plan's own grid, even n0): see below
+  const int ntx_max = (g.T[0] + 2) & ~1;
+  int next = 0;  // thread 0: the subproblem id claimed for the next iteration
+  if (threadIdx.x == 0) next = atomicAdd(work, 1);
 
   for (;;) {
-    if (threadIdx.x == 0) next_subproblem(g, s, bt, work, &s_sub, &s_bin, &s_goff, &s_geo);
+    if (threadIdx.x == 0) {
+      resolve_subproblem(g, s, bt, next, &s_sub, &s_bin, &s_goff, &s_geo);
+      next = atomicAdd(work, 1);  // in flight while this subproblem is worked on
+    }
     if (threadIdx.x < 8) hist[threadIdx.x] = 0;
     __syncthreads();
     const int sub = s_sub;
@@ -442,11 +458,35 @@ __global__ void __launch_bounds__(256, 4) k_interp_q(Geom g, const __grid_consta
     // one TMA box when the used part of the tile lies inside the grid (no periodic wrap)
     const bool by_tma = use_tmap && ox >= 0 && ox + tx <= n0 && org[1] >= 0 && org[1] + g.T[1] <= n1 &&
                         org[2] >= 0 && org[2] + g.T[2] <= n2;
+    // A tile that wraps: one bulk copy per row, or two where the row crosses the grid's x edge,
+    // of its cells [0, ntx) (data cells rounded up to even: ox and n0 even, so every piece starts
+    // 16-byte aligned and holds whole pairs of cells), all completing on the tile's mbarrier.
+    const bool by_rows = !by_tma && use_tmap && (n0 & 1) == 0 && ntx_max <= n0;
     if (by_tma) {
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
         mbar_expect_tx(&s_bar, tile_bytes);
         tma_load_3d(tile, &tmap, 2 * ox, org[1], org[2], &s_bar);
+      }
+    } else if (by_rows) {
+      const int ntx = (tx + 1) & ~1, nrows = g.T[1] * g.T[2];
+      if (threadIdx.x == 0) mbar_expect_tx(&s_bar, 8u * (unsigned)(ntx * nrows));
+      __syncthreads();  // the expected bytes are posted before any copy can complete
+      const float2* gridt = grid + s_goff;
+      fence_proxy_async_smem();
+      for (int row = threadIdx.x; row < nrows; row += blockDim.x) {
+        const int t1 = row % g.T[1], t2 = row / g.T[1];
+        const long long gy = wrap_idx(org[1] + t1, n1);
+        const long long gz = wrap_idx(org[2] + t2, n2);
+        const float2* grow = gridt + (gz * n1 + gy) * (long long)n0;
+        float2* trow = tile + (t2 * QT1 + t1) * S0;
+        if (ox >= 0 && ox + ntx <= n0) {
+          bulk_load(trow, grow + ox, 8u * ntx, &s_bar);
+        } else {
+          const int a = ox < 0 ? -ox : n0 - ox;  // cells before the edge
+          bulk_load(trow, grow + (ox < 0 ? ox + n0 : ox), 8u * a, &s_bar);
+          bulk_load(trow + a, grow, 8u * (ntx - a), &s_bar);
+        }
       }
     } else {
       const float2* gridt = grid + s_goff;
@@ -475,7 +515,7 @@ __global__ void __launch_bounds__(256, 4) k_interp_q(Geom g, const __grid_consta
         if (k < cnt) stage_point_q<W>(g, r[u], k, xsh, st, hist);
       }
     }
-    if (by_tma) {
+    if (by_tma || by_rows) {
       const bool ok = mbar_wait_bounded(&s_bar, phase);
       phase ^= 1u;
       if (__syncthreads_or(!ok)) {  // the copy never completed: report and stop this block
