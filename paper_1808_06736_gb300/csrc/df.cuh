@@ -3,7 +3,7 @@
 // 48 significant bits.  Products use the FMA error term, sums TwoSum (Knuth)
 // or FastTwoSum (Dekker); every operation is spelled with a rounding
 // intrinsic so the compiler contracts nothing.  Used where the GB300's FP64
-// rate (about 1/60 of FP32) would otherwise bind the complex128 path.
+// rate (about 1/64 of FP32) would otherwise bind the complex128 path.
 #pragma once
 
 namespace nufft {

@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(256, MinBlocks<T>::value) k_interp(Geom g, con
 }
 
 // ------------------------------------------------ interp, complex128
-// The GB300 runs FP64 at about 1/60 of its FP32 rate, so the complex128
+// The GB300 runs FP64 at about 1/64 of its FP32 rate, so the complex128
 // interpolation runs in double-float arithmetic on the FP32 pipe (df.cuh):
 // the kernel values (square root, exponential) and the w^d-term tensor
 // contraction; every tile value and weight is a pair (hi, lo) of floats with
