@@ -82,7 +82,10 @@ __device__ __forceinline__ void df_mac(DF& s, const DF a, const DF b) {
   s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, e));
 }
 
-// sqrt(a), a >= 0: the float root refined by one Newton step in double-float
+// sqrt(a), a >= 0: the float root refined by one Newton step in double-float.  The correction
+// (a - s0^2) / (2 s0) is about 2^-24 of the root, so an approximate division (relative error
+// ~2^-22) leaves an absolute error near 2^-48 in the result, the size of the rounding of a's
+// own double-float operations.
 __device__ __forceinline__ DF df_sqrt(DF a) {
   if (!(a.hi > 0.0f)) return DF{0.0f, 0.0f};
   const float s0 = __fsqrt_rn(a.hi);
@@ -90,30 +93,52 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
   const float pe = __fmaf_rn(s0, s0, -p);
   // residual a - s0^2, exact in its leading part
   const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
-  return df_quick(s0, __fdiv_rn(r, __fmul_rn(2.0f, s0)));
+  return df_quick(s0, __fdividef(r, __fmul_rn(2.0f, s0)));
 }
 
-// e^x for x <= 0 (x >= -100): x = k ln 2 + r, |r| <= ln(2)/2, e^r by its Taylor
-// series to degree 13 (remainder below 2e-16), then the exact scaling by 2^k.
+// e^x for -110 <= x <= 0 (x normalised).  Reduction x = k ln 2 + r, |r| <= ln(2)/2 + 2^-20, with
+// ln 2 = LN2_HI + LN2_MID + LN2_LO (16, 16 and 24 bits): for |k| < 2^7 the products k LN2_HI and
+// k LN2_MID are exact, x.hi - k LN2_HI is exact (Sterbenz), and two exact sums (TwoSum) add
+// x.lo and -k LN2_MID, so r is known to ~2^-50.  e^r by its Taylor series to degree 12
+// (remainder below 2e-16): the terms of degree 8..12 (at most 5e-9) in float, which costs them
+// no more than 2^-51, the terms of degree 0..7 by Horner steps in double-float, each adding the
+// float pair of 1/j! to r times the running value with FastTwoSum (|1/j!| exceeds the product)
+// and the result left unnormalised until the end.  Then the exact scaling by 2^k.  Relative
+// error ~2^-47.5 (checked against 120-bit arithmetic with the float operations emulated
+// exactly); about a third of the operations of the plain degree-13 double-float Horner scheme.
 __device__ __forceinline__ DF df_exp_neg(DF x) {
   const float k = rintf(__fmul_rn(x.hi, 1.44269504088896340736f));
-  // ln 2 = LN2_HI + LN2_LO with LN2_HI holding 16 bits, so k * LN2_HI is exact for |k| < 2^8
-  const float LN2_HI = 0.693145751953125f;
-  const float LN2_LO = 1.42860682030941723212e-6f;
-  DF r = df_add(x, DF{__fmul_rn(-k, LN2_HI), 0.0f});
-  r = df_add(r, df_mul(DF{-k, 0.0f}, DF{LN2_LO, 0.0f}));
-  // Horner with 1/j! for j = 13 .. 0, each as a pair of floats (hi, lo)
-  const float fh[14] = {1.000000000e+00f, 1.000000000e+00f, 5.000000000e-01f, 1.666666716e-01f, 4.166666791e-02f,
-                        8.333333768e-03f, 1.388888923e-03f, 1.984127011e-04f, 2.480158764e-05f, 2.755731884e-06f,
-                        2.755731998e-07f, 2.505210794e-08f, 2.087675588e-09f, 1.605904437e-10f};
-  const float fl[14] = {0.0f, 0.0f, 0.0f, -4.967053879e-09f, -1.241763470e-09f, -4.346172033e-10f,
-                        -3.363109444e-11f, -2.725596875e-12f, -3.406996094e-13f, 3.793571224e-14f,
-                        -7.575112209e-15f, 4.417623045e-16f, 1.108283981e-16f, -5.352526512e-18f};
-  DF y = DF{fh[13], fl[13]};
+  const float LN2_HI = 0x1.62e4p-1f;
+  const float LN2_MID = 0x1.7f7ep-20f;
+  const float LN2_LO = -1.2905320041778356e-11f;
+  const float a = __fmaf_rn(-k, LN2_HI, x.hi);  // exact
+  const DF s1 = df_two_sum(a, x.lo);
+  const DF s2 = df_two_sum(s1.hi, -__fmul_rn(k, LN2_MID));  // k LN2_MID exact
+  const DF r = df_quick(s2.hi, __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fmul_rn(-k, LN2_LO)));
+  // 1/j! for j = 0..7 as float pairs (hi, lo); j = 8..12 as floats
+  const float fh[8] = {1.0f, 1.0f, 0.5f, 1.666666716e-01f, 4.166666791e-02f, 8.333333768e-03f, 1.388888923e-03f,
+                       1.984127011e-04f};
+  const float fl[8] = {0.0f, 0.0f, 0.0f, -4.967053879e-09f, -1.241763470e-09f, -4.346172033e-10f,
+                       -3.363109444e-11f, -2.725596875e-12f};
+  float t = 2.087675588e-09f;  // 1/12!
+  t = __fmaf_rn(t, r.hi, 2.505210794e-08f);
+  t = __fmaf_rn(t, r.hi, 2.755731998e-07f);
+  t = __fmaf_rn(t, r.hi, 2.755731884e-06f);
+  t = __fmaf_rn(t, r.hi, 2.480158764e-05f);
+  DF y = {t, 0.0f};
 #pragma unroll
-  for (int j = 12; j >= 0; --j) y = df_add(df_mul(y, r), DF{fh[j], fl[j]});
-  const int ki = (int)k;
-  return DF{ldexpf(y.hi, ki), ldexpf(y.lo, ki)};
+  for (int j = 7; j >= 0; --j) {
+    const float p = __fmul_rn(r.hi, y.hi);
+    float e = __fmaf_rn(r.hi, y.hi, -p);
+    e = __fmaf_rn(r.hi, y.lo, e);
+    e = __fmaf_rn(r.lo, y.hi, e);
+    const float sh = __fadd_rn(fh[j], p);
+    const float err = __fsub_rn(p, __fsub_rn(sh, fh[j]));
+    y = DF{sh, __fadd_rn(err, __fadd_rn(e, fl[j]))};
+  }
+  y = df_norm(y);
+  const float sc = __int_as_float(((int)k + 127) << 23);  // 2^k, normal for k >= -126
+  return DF{__fmul_rn(y.hi, sc), __fmul_rn(y.lo, sc)};
 }
 
 // The ES kernel (Eq. (ES)) exp(beta (sqrt(1 - z^2) - 1)) in double-float; with cosh_kernel
