@@ -18,6 +18,16 @@ __device__ __forceinline__ DF df_of(double x) {
 }
 __device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
 
+// k[i] for a run-time i < N, by predicated moves over a register array
+template <int N>
+__device__ __forceinline__ DF df_pick(const DF* k, int i) {
+  DF v = k[0];
+#pragma unroll
+  for (int t = 1; t < N; ++t)
+    if (i == t) v = k[t];
+  return v;
+}
+
 // ilogb(|x|) + 1 of a normal double from its exponent field; -1100 for zero, subnormals,
 // infinities and NaN, which take no part in a tile's scale
 __device__ __forceinline__ int df_bexp(double x) {

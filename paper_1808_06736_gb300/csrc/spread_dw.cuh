@@ -215,9 +215,12 @@ __global__ void __launch_bounds__(DWords::kThreads, 1) k_spread_dw(Geom g, const
             k2 = es_eval_df_z(z, bdf, COSH);
           }
           const DF cr2 = df_mul(cr, k2), ci2 = df_mul(ci, k2);
-#pragma unroll
+          // rows one at a time (the row's y value picked from registers): the fully unrolled w^2
+          // rows of w cells overflowed the instruction cache (ncu: 1.1 no-instruction stalls per issue)
+#pragma unroll 1
           for (int l1 = 0; l1 < W1; ++l1) {
-            const DF cr1 = df_mul(cr2, k1[l1]), ci1 = df_mul(ci2, k1[l1]);
+            const DF k1v = df_pick<(D > 1) ? W : 1>(k1, l1);
+            const DF cr1 = df_mul(cr2, k1v), ci1 = df_mul(ci2, k1v);
             const int o = base + l1 * T0 + l2 * T01;
 #pragma unroll
             for (int l0 = 0; l0 < W; ++l0) {

@@ -916,8 +916,11 @@ __global__ void __launch_bounds__(kInterpDfThreads, 1) k_interp_df(Geom g, const
 #pragma unroll 1
       for (int l2 = 0; l2 < W2; ++l2) {
         DF br = {0.f, 0.f}, bi = {0.f, 0.f};
-#pragma unroll
+        // rows one at a time (the row's y value picked from registers): the fully unrolled w^2
+        // rows of w cells overflowed the instruction cache (ncu: 1.2 no-instruction stalls per issue)
+#pragma unroll 1
         for (int l1 = 0; l1 < W1; ++l1) {
+          const DF k1v = df_pick<(D > 1) ? W : 1>(k1, l1);
           const float4* rowp = tdf + base + l1 * T0 + l2 * T01;
           // even and odd nodes in separate accumulators: four independent
           // dependency chains per point instead of two
@@ -934,8 +937,8 @@ __global__ void __launch_bounds__(kInterpDfThreads, 1) k_interp_df(Geom g, const
             }
           }
           const DF sr = df_add(df_norm(sr0), df_norm(sr1)), si = df_add(df_norm(si0), df_norm(si1));
-          df_mac(br, sr, k1[l1]);
-          df_mac(bi, si, k1[l1]);
+          df_mac(br, sr, k1v);
+          df_mac(bi, si, k1v);
         }
         DF k2 = {1.0f, 0.0f};
         if constexpr (D > 2) k2 = es_eval_df(node_z<W>(l2, st2, f2), bdf, COSH);
