@@ -41,9 +41,10 @@ struct Geom {
 __host__ __device__ __forceinline__ bool quad_layout(const Geom& g) { return g.qs0 > 0; }
 // Dynamic shared memory of the bank-grouped complex64 kernels (each with 128 bytes of slack to
 // align the tile for TMA).  Spread: re and im planes of qtile ints, maxsub staged strengths, the
-// point order (5 maxsub shorts).  Interp: the tile (qtile float2), the point order.
+// gapless point order (3 maxsub shorts).  Interp: the tile (qtile float2), the point order.
 __host__ __device__ inline size_t spread_q_bytes(const Geom& g) {
-  return 128 + 2 * (size_t)g.qtile * 4 + (size_t)g.maxsub * 8 + (size_t)g.maxsub * 5 * 2;
+  // the spread's gapless point order needs 3 maxsub shorts (the interpolation's aligned one 5)
+  return 128 + 2 * (size_t)g.qtile * 4 + (((size_t)g.maxsub * 8 + (size_t)g.maxsub * 3 * 2 + 15) & ~(size_t)15);
 }
 __host__ __device__ inline size_t interp_q_bytes(const Geom& g) {
   return 128 + (size_t)g.qtile * 8 + (size_t)g.maxsub * 5 * 2;

@@ -196,17 +196,18 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Flush of a tile that lies inside the grid: the fixed-point planes are converted in place to
-// (re, im) float pairs (each thread holds up to kFlushCells of its cells in registers across
-// one barrier) and added to the grid by one bulk tensor reduction of the whole box.  Cells that
-// hold 0 give exactly 0 (also when inv is NaN, as in the per-cell flush).  The caller waits
-// (bulk_wait_read) before the tile is written again.
+// (re, im) float pairs (each thread holds a run of up to kFlushCells consecutive cells in
+// registers across one barrier) and added to the grid by one bulk tensor reduction of the whole
+// box.  Cells that hold 0 give exactly 0 (also when inv is NaN, as in the per-cell flush).  The
+// caller waits (bulk_wait_read) before the tile is written again.
 constexpr int kFlushCells = 19;
 __device__ __forceinline__ void flush_tile_tma(int* tre, int qtile, float inv, const CUtensorMap* map, int x, int y,
                                                int z) {
   int re[kFlushCells], im[kFlushCells];
+  const int c0 = threadIdx.x * kFlushCells;  // odd run length: the runs of a warp fall in distinct banks
 #pragma unroll
   for (int k = 0; k < kFlushCells; ++k) {
-    const int c = threadIdx.x + k * blockDim.x;
+    const int c = c0 + k;
     re[k] = c < qtile ? tre[c] : 0;
     im[k] = c < qtile ? tre[qtile + c] : 0;
   }
@@ -214,7 +215,7 @@ __device__ __forceinline__ void flush_tile_tma(int* tre, int qtile, float inv, c
   float2* t2 = reinterpret_cast<float2*>(tre);
 #pragma unroll
   for (int k = 0; k < kFlushCells; ++k) {
-    const int c = threadIdx.x + k * blockDim.x;
+    const int c = c0 + k;
     if (c < qtile) t2[c] = make_float2(re[k] ? float(re[k]) * inv : 0.f, im[k] ? float(im[k]) * inv : 0.f);
   }
   fence_proxy_async_smem();
@@ -226,8 +227,82 @@ __device__ __forceinline__ void flush_tile_tma(int* tre, int qtile, float inv, c
 }
 
 // ------------------------------------------------------------ quad spread
-// Shared memory (spread_q_bytes): re and im planes of qtile ints, the staged strengths
-// (maxsub float2), the aligned point order (5 maxsub shorts).
+// Shared memory (spread_q_bytes): re and im planes of qtile ints (128-byte aligned), the staged
+// strengths (maxsub float2), the gapless point order (3 maxsub shorts).
+
+// One pass of a subproblem's points over the tile (the main loop of k_spread_q).
+template <int W>
+__device__ __forceinline__ void spread_pass_q(const Geom& g, const KEval<float, W>& ke, const RecF* __restrict__ rec,
+                                              int p0, const Stage<float, 3>& st, const float2* sc, int nslots,
+                                              int npass, int pass, float thr, float scale, int xsh, unsigned tre_s,
+                                              int qtile) {
+  constexpr bool kPar = (W % 4) == 2;
+  constexpr int YSTEP = kPar ? 2 : 4, ZSTEP = kPar ? 2 : 1;
+  constexpr int NA = W / YSTEP, NB = W / ZSTEP;  // y and z nodes per lane
+  constexpr int NS = (W + 3) / 4;                // nodes per lane of a shared row (t = q mod 4)
+  const int S0 = g.qs0, S01 = g.qs0 * g.qt1;
+  const int lane = threadIdx.x & 31, p = lane >> 2, q = lane & 3;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int qb = lane & ~3;  // first lane of this point's quad
+  const int yq0 = kPar ? (q & 1) : q, zq0 = kPar ? (q >> 1) : 0;
+  const int loff = yq0 * S0 + zq0 * S01;
+  const int ngroups = (nslots + 7) >> 3;
+  for (int gi = wid; gi < ngroups; gi += nw) {  // warp-uniform trip count: shuffles below see all lanes
+    const int sl = gi * 8 + p;
+    int qi = sl < nslots ? (int)st.order[sl] : (int)kEmptySlot;
+    if (npass == 2 && qi != kEmptySlot) {  // this pass's strengths only
+      const float2 cq = sc[qi];
+      if ((fmaxf(fabsf(cq.x), fabsf(cq.y)) > thr) != (pass == 0)) qi = kEmptySlot;
+    }
+    const bool act = qi != kEmptySlot;
+    RecF r;
+    r.v[0] = r.v[1] = r.v[2] = 0.f;
+    if (act) r = rec[p0 + qi];
+    int sx, sy, sz, ts0, ts1, ts2;
+    float fx, fy, fz;
+    coord_cell<W>(r.v[0], g.B[0], sx, ts0, fx);
+    coord_cell<W>(r.v[1], g.B[1], sy, ts1, fy);
+    coord_cell<W>(r.v[2], g.B[2], sz, ts2, fz);
+    // x values: lane q evaluates nodes t = q (mod 4), the quad exchanges them
+    float kq[NS], k0[W];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) kq[u] = (q + 4 * u < W) ? es_node_q<W>(ke, q + 4 * u, sx, fx) : 0.f;
+#pragma unroll
+    for (int t = 0; t < W; ++t) k0[t] = __shfl_sync(0xffffffffu, kq[t / 4], qb + (t & 3));
+    float K2[NB];
+    if constexpr (kPar) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) K2[b] = es_node_q<W>(ke, zq0 + ZSTEP * b, sz, fz);
+    } else {  // every z node: evaluated t = q (mod 4) and exchanged like x
+#pragma unroll
+      for (int u = 0; u < NS; ++u) kq[u] = (q + 4 * u < W) ? es_node_q<W>(ke, q + 4 * u, sz, fz) : 0.f;
+#pragma unroll
+      for (int t = 0; t < W; ++t) K2[t] = __shfl_sync(0xffffffffu, kq[t / 4], qb + (t & 3));
+    }
+    if (!act) continue;
+    float K1[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) K1[a] = es_node_q<W>(ke, yq0 + YSTEP * a, sy, fy);
+    const float2 cv = sc[qi];
+    const float cr = cv.x * scale, ci = cv.y * scale;
+    const unsigned pr = tre_s + 4u * (unsigned)(ts0 + xsh + S0 * ts1 + S01 * ts2 + loff);
+    const unsigned pi = pr + 4u * (unsigned)qtile;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const float cr2 = cr * K2[b], ci2 = ci * K2[b];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        const float cr1 = cr2 * K1[a], ci1 = ci2 * K1[a];
+        const unsigned off = 4u * (unsigned)(YSTEP * a * S0 + ZSTEP * b * S01);
+#pragma unroll
+        for (int l0 = 0; l0 < W; ++l0) {
+          red_shared(pr + off + 4u * l0, Fixed<float>::bits(Fixed<float>::quant_fma(cr1, k0[l0])));
+          red_shared(pi + off + 4u * l0, Fixed<float>::bits(Fixed<float>::quant_fma(ci1, k0[l0])));
+        }
+      }
+    }
+  }
+}
 
 template <int W>
 __global__ void __launch_bounds__(256, 4) k_spread_q(Geom g, const __grid_constant__ KEval<float, W> ke, Sorted s,
@@ -239,29 +314,20 @@ __global__ void __launch_bounds__(256, 4) k_spread_q(Geom g, const __grid_consta
   //   w = 0 (mod 4): l1 = q (mod 4), every l2             -- w/4 x w rows.
   // Its row offset yq0 qs0 + zq0 qs01 is 0, 8, 16 or 24 banks (mod 32) from lane 0's, and
   // the remaining row offsets (multiples of ystep, zstep) are the same for the four lanes.
-  constexpr bool kPar = (W % 4) == 2;
-  constexpr int YSTEP = kPar ? 2 : 4, ZSTEP = kPar ? 2 : 1;
-  constexpr int NA = W / YSTEP, NB = W / ZSTEP;  // y and z nodes per lane
-  constexpr int NS = (W + 3) / 4;                // nodes per lane of a shared row (t = q mod 4)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int hist[8];
   __shared__ int s_sub, s_bin, s_nslots, s_maxbits, s_nsmall, s_msmall;
   __shared__ long long s_goff;
   __shared__ Geom s_geo;
 
-  const int qtile = g.qtile, maxsub = g.maxsub, S0 = g.qs0, S01 = g.qs0 * g.qt1;
+  const int qtile = g.qtile, maxsub = g.maxsub;
   // the tile starts 128-byte aligned: the source of the bulk tensor reduction
   int* tre = reinterpret_cast<int*>(smem + ((128u - (smem_u32(smem) & 127u)) & 127u));
   int* tim = tre + qtile;
   float2* sc = reinterpret_cast<float2*>(tim + qtile);
   Stage<float, 3> st = carve_stage<float, 3>(reinterpret_cast<unsigned char*>(sc + maxsub), maxsub);
   const RecF* __restrict__ rec = reinterpret_cast<const RecF*>(s.rec);
-  const int lane = threadIdx.x & 31, p = lane >> 2, q = lane & 3;
-  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int qb = lane & ~3;  // first lane of this point's quad
   const unsigned tre_s = smem_u32(tre);
-  const int yq0 = kPar ? (q & 1) : q, zq0 = kPar ? (q >> 1) : 0;
-  const int loff = yq0 * S0 + zq0 * S01;
 
   // tiles flushed by one bulk reduction: whole tile inside the grid, the plan's own grid
   const bool tma_ok = use_tmap && bt.B == 0 && qtile <= kFlushCells * (int)blockDim.x;
@@ -339,63 +405,7 @@ __global__ void __launch_bounds__(256, 4) k_spread_q(Geom g, const __grid_consta
       }
       float scale, inv;
       pass_scale(K, pass == 0 ? maxabs : smax, &scale, &inv);
-
-      const int ngroups = (nslots + 7) >> 3;
-      for (int gi = wid; gi < ngroups; gi += nw) {  // warp-uniform trip count: shuffles below see all lanes
-        const int sl = gi * 8 + p;
-        int qi = sl < nslots ? (int)st.order[sl] : (int)kEmptySlot;
-        if (npass == 2 && qi != kEmptySlot) {  // this pass's strengths only
-          const float2 cq = sc[qi];
-          if ((fmaxf(fabsf(cq.x), fabsf(cq.y)) > thr) != (pass == 0)) qi = kEmptySlot;
-        }
-        const bool act = qi != kEmptySlot;
-        RecF r;
-        r.v[0] = r.v[1] = r.v[2] = 0.f;
-        if (act) r = rec[p0 + qi];
-        int sx, sy, sz, ts0, ts1, ts2;
-        float fx, fy, fz;
-        coord_cell<W>(r.v[0], g.B[0], sx, ts0, fx);
-        coord_cell<W>(r.v[1], g.B[1], sy, ts1, fy);
-        coord_cell<W>(r.v[2], g.B[2], sz, ts2, fz);
-        // x values: lane q evaluates nodes t = q (mod 4), the quad exchanges them
-        float kq[NS], k0[W];
-  #pragma unroll
-        for (int u = 0; u < NS; ++u) kq[u] = (q + 4 * u < W) ? es_node_q<W>(ke, q + 4 * u, sx, fx) : 0.f;
-  #pragma unroll
-        for (int t = 0; t < W; ++t) k0[t] = __shfl_sync(0xffffffffu, kq[t / 4], qb + (t & 3));
-        float K2[NB];
-        if constexpr (kPar) {
-  #pragma unroll
-          for (int b = 0; b < NB; ++b) K2[b] = es_node_q<W>(ke, zq0 + ZSTEP * b, sz, fz);
-        } else {  // every z node: evaluated t = q (mod 4) and exchanged like x
-  #pragma unroll
-          for (int u = 0; u < NS; ++u) kq[u] = (q + 4 * u < W) ? es_node_q<W>(ke, q + 4 * u, sz, fz) : 0.f;
-  #pragma unroll
-          for (int t = 0; t < W; ++t) K2[t] = __shfl_sync(0xffffffffu, kq[t / 4], qb + (t & 3));
-        }
-        if (!act) continue;
-        float K1[NA];
-  #pragma unroll
-        for (int a = 0; a < NA; ++a) K1[a] = es_node_q<W>(ke, yq0 + YSTEP * a, sy, fy);
-        const float2 cv = sc[qi];
-        const float cr = cv.x * scale, ci = cv.y * scale;
-        const unsigned pr = tre_s + 4u * (unsigned)(ts0 + xsh + S0 * ts1 + S01 * ts2 + loff);
-        const unsigned pi = pr + 4u * (unsigned)qtile;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const float cr2 = cr * K2[b], ci2 = ci * K2[b];
-#pragma unroll
-          for (int a = 0; a < NA; ++a) {
-            const float cr1 = cr2 * K1[a], ci1 = ci2 * K1[a];
-            const unsigned off = 4u * (unsigned)(YSTEP * a * S0 + ZSTEP * b * S01);
-#pragma unroll
-            for (int l0 = 0; l0 < W; ++l0) {
-              red_shared(pr + off + 4u * l0, Fixed<float>::bits(Fixed<float>::quant_fma(cr1, k0[l0])));
-              red_shared(pi + off + 4u * l0, Fixed<float>::bits(Fixed<float>::quant_fma(ci1, k0[l0])));
-            }
-          }
-        }
-      }
+      spread_pass_q<W>(g, ke, rec, p0, st, sc, nslots, npass, pass, thr, scale, xsh, tre_s, qtile);
       __syncthreads();
       const int ox = org[0] - xsh;
       if (tma_ok && ox >= 0 && ox + g.T[0] + xsh <= s_geo.n[0] && org[1] >= 0 && org[1] + g.T[1] <= s_geo.n[1] &&
