@@ -36,14 +36,14 @@ sys.path.insert(0, ROOT)
 METRIC = "type1/2 NU points/s at eps=1e-5 (3D, fp32)"
 
 # DRAM bytes (read + write) per launch of the spread / interp kernels on the
-# default workload: the bytes per point of a full-ncu-set capture of the same kernels on
-# 1e7 points (a 256^3 fine grid, similar points per cell) times 1e8 points -- valid only
-# for the kernel source they were measured on.
+# default workload: the bytes of an ncu capture of the same kernels on 1e7 points (a 256^3
+# fine grid, similar points per cell; DRAM bytes per second times the launch's duration)
+# times 10 for 1e8 points -- valid only for the kernel source they were measured on.
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1808_06736_gb300", "csrc", "spread_interp_q.cuh")
 MEASURED_TRAFFIC = {
-    "sha256": "175d8a4b4ffb44426f95d25d01961e6ab98b90a2a4dc66e02f60db6dcf95e6c8",
-    "spread": (1084197000 + 96837632) * 10,
-    "interp": (481178000 + 234544640) * 10,
+    "sha256": "b3390d078c38abf3414666daf5397155fec4e8e727a4103758261932d049f318",
+    "spread": 1181453716 * 10,
+    "interp": 723761629 * 10,
 }
 
 
