@@ -325,16 +325,21 @@ __device__ __forceinline__ int bucket_order(int cnt, Stage<T, D>& st, const int*
     __syncthreads();
     return cnt;
   }
+  // rounds below the smallest group's size hold a point of every group: each fills a slot group
+  // exactly (slot NRES r), so only the rounds from minsz on are packed one after another
+  int minsz = sz[0];
+#pragma unroll
+  for (int b = 1; b < NRES; ++b) minsz = min(minsz, sz[b]);
   for (int r = threadIdx.x; r < maxsz; r += blockDim.x) {  // round sizes (maxsz <= cnt)
     int k = 0;
 #pragma unroll
     for (int b = 0; b < NRES; ++b) k += sz[b] > r ? 1 : 0;
-    st.rstart[r] = (unsigned short)k;
+    st.rstart[r] = (unsigned short)(r < minsz ? NRES * r : k);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int slot = 0, fill = 0;  // fill = slot mod NRES
-    for (int r = 0; r < maxsz; ++r) {
+    int slot = NRES * minsz, fill = 0;  // fill = slot mod NRES
+    for (int r = minsz; r < maxsz; ++r) {
       const int k = st.rstart[r];
       if (fill + k > NRES) {
         slot += NRES - fill;
