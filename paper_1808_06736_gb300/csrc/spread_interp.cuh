@@ -821,6 +821,9 @@ __device__ __forceinline__ void point_weights_df(double v, int B, DF beta, int c
   }
 }
 
+__device__ __forceinline__ double2 out_of(DF ar, DF ai, int sh) {
+  return make_double2(ldexp((double)ar.hi + (double)ar.lo, sh), ldexp((double)ai.hi + (double)ai.lo, sh));
+}
 // blocks of 512 threads: a tile of a 16x8x8 bin at w = 10 (135 KB) leaves room for one block
 // per SM, and 512 threads at up to 128 registers fill the register file
 constexpr int kInterpDfThreads = 512;
@@ -892,10 +895,24 @@ __global__ void __launch_bounds__(kInterpDfThreads, 1) k_interp_df(Geom g, const
     // order's extra (partly idle) warps cost more than its fewer bank conflicts save
     const int nslots = bucket_order<double, D, NRES_INTERP, false>(cnt, st, hist, &s_nslots);  // synchronises
 
-    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
-      const int q = st.order[sl];
-      if (q == kEmptySlot) continue;
-      const Rec rq = rec[p0 + q];
+    // a subproblem of fewer points than threads leaves most threads idle through the w^3 cells
+    // of a point: up to 8 threads share a point (3D), each summing every tpp-th plane of its
+    // stencil; the partial sums are added with shuffles (warp-uniform trip count)
+    int tpp = 1;
+    if constexpr (D == 3) {
+      while (tpp < 8 && tpp < W && 2 * tpp * nslots <= (int)blockDim.x) tpp *= 2;
+    }
+    const int ltpp = __ffs(tpp) - 1;
+    const int total = nslots << ltpp;
+    for (int u0 = threadIdx.x & ~31; u0 < total; u0 += blockDim.x) {
+      const int u = u0 + (threadIdx.x & 31);
+      const int part = u & (tpp - 1);
+      const int q = u < total ? (int)st.order[u >> ltpp] : (int)kEmptySlot;
+      const bool act = q != kEmptySlot;
+      Rec rq;
+      rq.v[0] = rq.v[1] = rq.v[2] = 0.0;
+      rq.idx = 0;
+      if (act) rq = rec[p0 + q];
       DF k0[W];
       int ts0, ts1 = 0, ts2 = 0;
       point_weights_df<W>(rq.v[0], g.B[0], bdf, COSH, ts0, k0);
@@ -919,7 +936,7 @@ __global__ void __launch_bounds__(kInterpDfThreads, 1) k_interp_df(Geom g, const
       constexpr int W2 = (D > 2) ? W : 1;
       DF ar = {0.f, 0.f}, ai = {0.f, 0.f};
 #pragma unroll 1
-      for (int l2 = 0; l2 < W2; ++l2) {
+      for (int l2 = act ? part : W2; l2 < W2; l2 += tpp) {
         DF br = {0.f, 0.f}, bi = {0.f, 0.f};
         // rows one at a time (the row's y value picked from registers): the fully unrolled w^2
         // rows of w cells overflowed the instruction cache (ncu: 1.2 no-instruction stalls per issue)
@@ -950,8 +967,13 @@ __global__ void __launch_bounds__(kInterpDfThreads, 1) k_interp_df(Geom g, const
         df_mac(ar, df_norm(br), k2);
         df_mac(ai, df_norm(bi), k2);
       }
-      const double2 out = make_double2(ldexp((double)ar.hi + (double)ar.lo, sh), ldexp((double)ai.hi + (double)ai.lo, sh));
-      store_once(c + rq.idx, out);
+      for (int o = 1; o < tpp; o <<= 1) {  // tpp is block-uniform: every lane shuffles
+        const DF pr = {__shfl_xor_sync(0xffffffffu, ar.hi, o), __shfl_xor_sync(0xffffffffu, ar.lo, o)};
+        const DF pi = {__shfl_xor_sync(0xffffffffu, ai.hi, o), __shfl_xor_sync(0xffffffffu, ai.lo, o)};
+        ar = df_add(df_norm(ar), df_norm(pr));
+        ai = df_add(df_norm(ai), df_norm(pi));
+      }
+      if (act && part == 0) store_once(c + rq.idx, out_of(ar, ai, sh));
     }
     __syncthreads();
   }
