@@ -106,7 +106,10 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
   return df_quick(s0, __fdividef(r, __fmul_rn(2.0f, s0)));
 }
 
-// e^x for -110 <= x <= 0 (x normalised).  Reduction x = k ln 2 + r, |r| <= ln(2)/2 + 2^-20, with
+// e^x for -87 <= x <= 0 (x normalised; 2^k stays a normal float), to ~2^-47.5 relative for
+// x >= -60 (below, the low part of the result nears the float underflow; the kernels evaluate
+// x >= -2 beta >= -74, where such values lie below 1e-26).  Reduction x = k ln 2 + r,
+// |r| <= ln(2)/2 + 2^-20, with
 // ln 2 = LN2_HI + LN2_MID + LN2_LO (16, 16 and 24 bits): for |k| < 2^7 the products k LN2_HI and
 // k LN2_MID are exact, x.hi - k LN2_HI is exact (Sterbenz), and two exact sums (TwoSum) add
 // x.lo and -k LN2_MID, so r is known to ~2^-50.  e^r by its Taylor series to degree 12
