@@ -16,7 +16,8 @@ nearest float, ties to even) with rational arithmetic:
     coefficients) are read from the kernel source, so the check follows the shipped code.
 
 Both emulations follow the operation sequence of paper_1808_06736_gb300/csrc/spread_dw.cuh
-(dw_split) and csrc/df.cuh (df_exp_neg) step by step.
+(dw_split) and csrc/df.cuh (df_exp_neg) step by step.  A third check covers the complex64
+spread's rounding of each contribution to an integer by one FMA (spread_interp.cuh, Fixed<float>).
 """
 import os
 import random
@@ -190,3 +191,20 @@ def test_double_float_exponential_relative_error():
         rel = abs((Decimal(yh) + Decimal(yl)) - ex) / ex
         worst = max(worst, float(rel))
     assert worst < 2.0 ** -46, worst
+
+
+def test_complex64_fixed_point_rounding():
+    """The complex64 spread's contribution: the bit pattern of fma(a, b, 1.5 2^23) minus that of
+    1.5 2^23 is a b rounded to the nearest integer, for |a b| below 2^22 (ties to even)."""
+    rng = random.Random(14)
+    for _ in range(3000):
+        a = rnd(F(rng.uniform(-1, 1) * 2.0 ** rng.uniform(0, 22)))
+        b = rnd(F(rng.uniform(0, 1)))
+        ex = F(a) * F(b)
+        if abs(ex) >= 2 ** 22:
+            continue
+        v = bits(fma(a, b, M)) - B
+        fl = ex.numerator // ex.denominator
+        rem = ex - fl
+        want = fl + (1 if rem > F(1, 2) or (rem == F(1, 2) and fl % 2 == 1) else 0)
+        assert v == want, (a, b, v, want)
