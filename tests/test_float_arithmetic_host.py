@@ -16,8 +16,10 @@ nearest float, ties to even) with rational arithmetic:
     coefficients) are read from the kernel source, so the check follows the shipped code.
 
 Both emulations follow the operation sequence of paper_1808_06736_gb300/csrc/spread_dw.cuh
-(dw_split) and csrc/df.cuh (df_exp_neg) step by step.  A third check covers the complex64
-spread's rounding of each contribution to an integer by one FMA (spread_interp.cuh, Fixed<float>).
+(dw_split) and csrc/df.cuh (df_exp_neg) step by step.  Two more checks cover the complex64
+path: the spread's rounding of each contribution to an integer by one FMA (spread_interp.cuh,
+Fixed<float>), and the binning's fold of a coordinate to (cell, fraction) with an FMA error term
+(binsort.cu, fold), accurate to 1e-7 cells.
 """
 import os
 import random
@@ -208,3 +210,44 @@ def test_complex64_fixed_point_rounding():
         rem = ex - fl
         want = fl + (1 if rem > F(1, 2) or (rem == F(1, 2) and fl % 2 == 1) else 0)
         assert v == want, (a, b, v, want)
+
+
+def _fold(x, s_hi, s_lo, n):
+    """The complex64 fold of binsort.cu: u = x n / (2 pi) as (cell in [0, n), frac in [0, 1))."""
+    p = mul(x, s_hi)
+    e = fma(x, s_hi, -p)
+    corr = fma(x, s_lo, e)
+    fl = float(np.floor(p))
+    fr = add(sub(p, fl), corr)  # p - fl is exact
+    i = int(fl)
+    if fr < 0.0:
+        fr = add(fr, 1.0)
+        i -= 1
+    if fr >= 1.0:
+        fr = sub(fr, 1.0)
+        i += 1
+    return i % n, fr
+
+
+def test_fold_fraction_accuracy():
+    """The fold forms x n / (2 pi) in float with an FMA error term and a two-float split of
+    n / (2 pi); the fraction it gives is within 1e-7 cells of the exact value for |x| <= 3 pi
+    (a plain float product is off by up to 2^-24 |u|, ~6e-5 cells at u ~ 1000)."""
+    mpmath = __import__("pytest").importorskip("mpmath")
+    mpmath.mp.prec = 120
+    rng = random.Random(15)
+    for n in (27, 512, 2048, 4096):
+        s = mpmath.mpf(n) / (2 * mpmath.pi)
+        s_hi = rnd(F(float(s)))  # the host's (float)(double)(n / 2 pi), as make_fold_const forms it
+        s_lo = rnd(F(float(s - mpmath.mpf(s_hi))))
+        worst = 0.0
+        for it in range(400):
+            x = rnd(F(rng.uniform(-3, 3) * 3.141592653589793))
+            cell, fr = _fold(x, s_hi, s_lo, n)
+            assert 0 <= cell < n and 0.0 <= fr < 1.0
+            u = mpmath.mpf(x) * s
+            u = u - n * mpmath.floor(u / n)  # in [0, n)
+            d = abs((cell + mpmath.mpf(fr)) - u)
+            d = min(d, n - d)  # u near n folds to near 0
+            worst = max(worst, float(d))
+        assert worst < 1e-7, (n, worst)
