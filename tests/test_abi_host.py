@@ -181,3 +181,9 @@ def test_horner_coeffs_rejects_bad_args(lib):
     assert lib.nufft_horner_coeffs(1, 5.0)[0] == -1
     assert lib.nufft_horner_coeffs(17, 5.0)[0] == -1
     assert lib.nufft_horner_coeffs(6, 0.0)[0] == -1
+
+
+def test_setpts_from_rejects_null_plans(lib):
+    """nufft_setpts_from checks its plan arguments before any device work."""
+    import ctypes
+    assert lib.nufft_setpts_from(ctypes.c_void_p(0), ctypes.c_void_p(0)) == -1
